@@ -1,0 +1,395 @@
+"""Benchmark: EELS map pixel-slices/s of the linear S-matrix method on one GB300.
+
+A step is one pass of the whole hot path over the workload: build S_in (all
+depths), stream S_out backwards and contract every transition of every slice
+into the FP64 map.  value = n_scan * n_z / step time, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the method has no exchange step; replicas only): value = N * units / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import specimen as sp  # noqa: E402
+
+METRIC = "EELS map pixel-slices/s"
+UNIT = "pixel-slices/s"
+DEFAULT_WORKLOAD = "rocksalt_fp32"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
+SMS, FP32_LANES = 152, 128
+
+
+def _peaks():
+    try:
+        return json.load(open(PEAKS))
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the conventional algorithm, FP64, as it stands)
+# ---------------------------------------------------------------------------
+
+def _oracle_probe_sample(args):
+    name, iy, ix, slice_i = args
+    import specimen as sp_
+    from oracle import multislice as ms
+    wl = sp_.WORKLOADS[name]()
+    rx, ry = wl.scan_positions()
+    keep = [s for s in range(wl.n_sites) if wl.site_slice[s] == slice_i
+            and ms.axis_in_window(wl.site_x[s], rx[ix], wl.cell, wl.f)
+            and ms.axis_in_window(wl.site_y[s], ry[iy], wl.cell, wl.f)]
+    sub = wl.with_sites(keep)
+    c = {}
+    t0 = time.perf_counter()
+    ms.quadratic_map(sub, positions=[(iy, ix)], counter=c)
+    return time.perf_counter() - t0, c["steps"]
+
+
+def _full_probe_steps(wl, iy, ix):
+    """Multislice operations of one probe in the conventional algorithm (Sec. III count)."""
+    from oracle import multislice as ms
+    rx, ry = wl.scan_positions()
+    steps = wl.n_z
+    for s in range(wl.n_sites):
+        if (ms.axis_in_window(wl.site_x[s], rx[ix], wl.cell, wl.f)
+                and ms.axis_in_window(wl.site_y[s], ry[iy], wl.cell, wl.f)):
+            steps += wl.n_types * (wl.n_z - int(wl.site_slice[s]))
+    return steps
+
+
+def cpu_oracle_rate(wl_name, budget_procs=None):
+    """Pixel-slices/s of the FP64 conventional oracle on this host's cores.
+
+    Sample: one probe per worker process (spread over the scan), each running the
+    conventional algorithm with only the sites of one deep slice of its window,
+    so every worker does a few hundred multislice operations.  The cost of the
+    conventional algorithm is exactly linear in its multislice count, so the
+    full-workload rate is the sampled time per operation times the full count.
+    """
+    wl = sp.WORKLOADS[wl_name]()
+    cores = budget_procs or os.cpu_count() or 1
+    n_sx, n_sy = wl.scan[0], wl.scan[1]
+    slice_i = max(0, wl.n_z - 4)
+    jobs = []
+    for k in range(cores):
+        iy = (k * 7 + 3) % n_sy
+        ix = (k * 13 + 5) % n_sx
+        jobs.append((wl_name, iy, ix, slice_i))
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_probe_sample, jobs)
+    wall = time.perf_counter() - t0
+    per_step = sum(t for t, _ in res) / sum(s for _, s in res)   # seconds per op per core
+    full = np.mean([_full_probe_steps(wl, j[1], j[2]) for j in jobs])
+    # one core finishes a probe (n_z pixel-slices) in full * per_step seconds
+    rate = cores * wl.n_z / (full * per_step)
+    sample = (f"{cores} processes x 1 probe of {wl.name}, sites of slice {slice_i} only "
+              f"({sum(s for _, s in res)} multislice ops, {wall:.1f} s wall); rate scaled by "
+              f"the full per-probe count {full:.0f} ops")
+    return rate, cores, sample
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def _algorithmic(wl, n_in, n_out, prof):
+    """Algorithmic bytes / flops per launch of each kernel class (design notes)."""
+    n = wl.n
+    nh = n // 2
+    cplx = 8
+    out = {}
+    # row pass: read W + write Phi (n x n/2 per wave), store n/2 x n/2 per wave, read t once
+    for name, waves in (("row_pass", n_in), ("row_pass_adjoint", n_out)):
+        out[name] = ("hbm", waves * (2 * n * nh + nh * nh) * cplx + n * n * cplx)
+    for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out)):
+        out[name] = ("hbm", waves * 2 * n * nh * cplx)
+    return out
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_1908_07628_gb300 import build
+    build.build()
+    import paper_1908_07628_gb300 as g
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    wl = sp.WORKLOADS[args.workload]()
+    ctx = g.Context(dev)
+    stream = torch.cuda.current_stream()
+    vdev = torch.from_numpy(wl.vproj).cuda()
+    Hdev = torch.from_numpy(wl.H).cuda()
+    mdev = torch.zeros((wl.n_types, wl.scan[1], wl.scan[0]), dtype=torch.float64, device="cuda")
+
+    def step():
+        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
+        g.inelastic_map_for(ctx, sm, wl, precision=args.precision, H=Hdev, out=mdev, stream=stream)
+        sm.free()
+
+    n_in = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)
+    n_out = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ctx.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    ctx.profile_enable(False)
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    units = wl.n_scan * wl.n_z
+    value = world * units / (ms_step / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    vh = torch.from_numpy(wl.vproj).pin_memory().numpy()
+    Hh = torch.from_numpy(wl.H).pin_memory().numpy()
+    mh = torch.zeros((wl.n_types, wl.scan[1], wl.scan[0]), dtype=torch.float64).pin_memory().numpy()
+
+    def e2e_step():
+        sm = g.build_smatrix_for(ctx, wl, vproj=vh, stream=stream)
+        g.inelastic_map_for(ctx, sm, wl, precision=args.precision, H=Hh, out=mh, stream=stream)
+        sm.free()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    h2d = wl.vproj.nbytes + wl.H.nbytes + wl.n_sites * (3 * 4 + 2 * 8)
+    d2h = wl.n_types * wl.n_scan * 8
+
+    # quadratic algorithm on the same GPU, seeded probe sample, scaled per pixel-slice
+    quad = None
+    if rank == 0 and not args.no_quadratic:
+        rng = np.random.default_rng(16)
+        npos = min(args.quad_probes, wl.n_scan)
+        flat = rng.choice(wl.n_scan, size=npos, replace=False)
+        pos = [(int(i // wl.scan[0]), int(i % wl.scan[0])) for i in flat]
+        g.quadratic_reference_map_for(ctx, wl, positions=pos[:1], stream=stream)
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        _, qsteps = g.quadratic_reference_map_for(ctx, wl, positions=pos, stream=stream)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qs = q0.elapsed_time(q1) / 1e3
+        quad = {"value": npos * wl.n_z / qs, "unit": UNIT, "probes": npos,
+                "multislice_ops": qsteps, "sample": f"{npos} seeded probes of the same scan"}
+
+    # roofline of the dominant kernel (CUDA-event times of every launch in the timed region)
+    peaks = _peaks()
+    alg = _algorithmic(wl, n_in, n_out, prof)
+    tot = {k: v["ms"] for k, v in prof.items()}
+    dom = max(tot, key=tot.get) if tot else None
+    roof = None
+    if dom is not None:
+        launches = prof[dom]["launches"]
+        avg_s = prof[dom]["ms"] / launches / 1e3
+        if dom in alg and alg[dom][0] == "hbm":
+            achieved = alg[dom][1] / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+        else:
+            flops = contraction_flops(wl, n_in, n_out, dom)
+            mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+            achieved = flops / launches / avg_s / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
+    share = {k: {"launches": prof[k]["launches"], "ms_per_step": prof[k]["ms"] / args.steps,
+                 "share": prof[k]["ms"] / max(sum(tot.values()), 1e-9)} for k in prof}
+    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "n_in": n_in,
+                   "n_out": n_out, "scan": [wl.scan[0], wl.scan[1]], "n_types": wl.n_types,
+                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (S_in alone is "
+                         f"{wl.n_z * n_in * (wl.n // 2) ** 2 * 8 / 1e9:.1f} GB)"},
+        "e2e": {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": roof,
+        "kernels": share,
+        "clocks": clk,
+        "gpu_quadratic": quad,
+    }
+    return line
+
+
+def contraction_flops(wl, n_in, n_out, kernel):
+    """Real flops of the contraction kernels over the whole workload (8 per complex MAC)."""
+    from oracle import multislice as ms   # window rule only, to count work
+    rx, ry = wl.scan_positions()
+    g1 = g2 = 0
+    for s in range(wl.n_sites):
+        nx = int(ms.axis_in_window(wl.site_x[s], rx, wl.cell, wl.f).sum())
+        ny = int(ms.axis_in_window(wl.site_y[s], ry, wl.cell, wl.f).sum())
+        if nx and ny:
+            g1 += wl.n_types * n_out * wl.w * wl.w * n_in
+            g2 += wl.n_types * n_out * n_in * nx * ny
+    return 8.0 * (g1 if "gemm1" in kernel else g2)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    wl = sp.WORKLOADS[args.workload]()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(args.workload)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, cores, sample = cpu_oracle_rate(args.workload)
+        vals.append(rate)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wl.n_scan * wl.n_z / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sp.WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--quad-probes", type=int, default=8)
+    ap.add_argument("--no-quadratic", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = reference_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    # the CPU sample forks worker processes: run it before the first CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(args.workload)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = gpu_arm(args, rank, world)
+    line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

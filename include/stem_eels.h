@@ -1,0 +1,184 @@
+/*
+ * stem_eels.h -- C ABI of the GB300 STEM-EELS library (libstemeels.so).
+ *
+ * Linear-scaling (PRISM) STEM-EELS maps after Brown, Ciston & Ophus,
+ * arXiv 1908.07628.  The library builds the probe-side scattering matrix S_in
+ * (Sec. III: "S_1 ... propagate the plane wave components that fall within the
+ * probe forming aperture"), carries the detector plane waves backwards to make
+ * S_out (Eq. MSTop, used as its complex conjugate), contracts
+ * M_n = S_out^H diag(H_n) S_in per transition (Eqs. Hn0op, SHn0) and
+ * accumulates f^2 sum_d |M_n a(R)|^2 into an FP64 map (second algorithm
+ * listing of Sec. III).  It also runs the conventional quadratic algorithm
+ * (first listing of Sec. III) on the GPU as the same-hardware baseline.
+ *
+ * Conventions shared by every call
+ * - Square cell L x L (Angstrom) sampled on an N x N grid, N = 2^a 3^b with
+ *   N in {64, 128, 256, 384, 512, 768, 1024}.  Real-space arrays are row-major
+ *   [y][x]; pixel (ix, iy) sits at (ix L/N, iy L/N).
+ * - Forward transform exp(-2 pi i r.g) (footnote to Eq. 4); the propagator is
+ *   band-limited to p^2 + q^2 < (N/4)^2 (Sec. III, "bandwidth limited ... to 1/2").
+ * - Probe beams: k = f(p, q)/L with lambda |k| <= alpha; detector beams the same
+ *   with beta.  Transition windows live on the N/2 grid.
+ * - Complex data are interleaved float pairs (re, im) -- "complex64".
+ * - Every pointer argument is borrowed for the duration of the call only.  A
+ *   flag next to each array says whether it is host or device memory; device
+ *   pointers must belong to the context's device.  Handles are owned by the
+ *   library and released by the matching _free / _destroy call.
+ * - Work is issued on the CUDA stream passed as `stream` (a cudaStream_t, NULL
+ *   for the legacy default stream).  Calls that return results to host memory
+ *   synchronise that stream before returning; calls that write device memory
+ *   return once the work is queued.
+ * - Errors: every call returns an eels_status; no call aborts or throws.  The
+ *   text of the last error of a context is available from eels_last_error().
+ */
+#ifndef STEM_EELS_H
+#define STEM_EELS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EELS_OK = 0,
+  EELS_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, beam outside band limit) */
+  EELS_ERR_UNSUPPORTED = 2,  /* grid size or option not built into this library */
+  EELS_ERR_OOM = 3,          /* device allocation failed */
+  EELS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  EELS_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+} eels_status;
+
+/* Arithmetic of the inelastic contraction (Eq. SHn0 and the |.|^2 scan sum).
+ * The multislice always runs in FP32 with FP64 propagator phases; the map is
+ * always accumulated in FP64. */
+typedef enum {
+  EELS_PREC_FP32 = 0,        /* FP32 CUDA-core complex GEMMs */
+  EELS_PREC_TF32 = 1,        /* tcgen05 TF32 tensor cores, FP32 accumulate */
+  EELS_PREC_BF16X3 = 2       /* tcgen05 BF16 hi+lo split (3 products), FP32 accumulate */
+} eels_precision;
+
+typedef struct eels_ctx eels_ctx;
+typedef struct eels_smatrix eels_smatrix;
+
+/* Specimen: the projected potential of each slice (Eq. 3-4, v_i(r) in V*A). */
+typedef struct {
+  int n;                  /* grid side N */
+  int n_z;                /* number of slices */
+  double cell;            /* L, Angstrom */
+  const float* vproj;     /* [n_z][n][n] V*A */
+  int vproj_on_device;    /* 1: device pointer, 0: host pointer */
+} eels_specimen;
+
+/* Electron optics of the probe and the PRISM interpolation (Sec. II-III). */
+typedef struct {
+  double lambda;          /* relativistic wavelength, Angstrom */
+  double sigma;           /* interaction constant, rad / (V A) */
+  double dz;              /* slice thickness, Angstrom */
+  int f;                  /* PRISM interpolation factor, >= 1 */
+  double alpha;           /* probe convergence semi-angle, rad */
+} eels_optics;
+
+/* Ionising sites and their transition potentials H_n0 (Eq. Hn0def), sampled on
+ * a w x w window of the N/2 grid whose origin (win_x0, win_y0) is periodic.
+ * (x, y) is the site position used for the PRISM window rule: a site counts
+ * for probe R iff the minimum-image r_s - R lies in [-L/2f, L/2f) on both axes. */
+typedef struct {
+  int n_sites;
+  int n_types;            /* channels per site (e.g. m = -1, 0, 1) */
+  int w;                  /* window side on the N/2 grid, 1 <= w <= N/2 */
+  const float* H;         /* complex64 [n_sites][n_types][w][w] */
+  const int32_t* slice;   /* [n_sites] slice index of each site */
+  const int32_t* win_x0;  /* [n_sites] window origin column on the N/2 grid */
+  const int32_t* win_y0;  /* [n_sites] window origin row */
+  const double* x;        /* [n_sites] Angstrom */
+  const double* y;        /* [n_sites] Angstrom */
+  int on_device;          /* 1: H is a device pointer (the small per-site arrays are always host) */
+} eels_transitions;
+
+/* Scan raster: R(ix, iy) = (x0 + ix*step_x, y0 + iy*step_y), Angstrom. */
+typedef struct {
+  int n_sx, n_sy;
+  double x0, y0, step_x, step_y;
+} eels_scan;
+
+/* Create a context on CUDA device `device`.  Owns twiddle tables and scratch. */
+eels_status eels_create(int device, eels_ctx** out);
+void eels_destroy(eels_ctx* ctx);
+/* Text of the last error raised on this context ("" if none).  Owned by ctx. */
+const char* eels_last_error(const eels_ctx* ctx);
+
+/* Build S_in (Sec. III second listing, "Advance S_1 one slice"): the plane
+ * waves of the probe aperture on the f-lattice carried through slices
+ * 0..n_z-1; S_in(i) = Dec(t_i psi_j(i)) is stored for every depth on the N/2
+ * grid as complex64 [n_z][n_in][N/2][N/2] (beam-major planes), scaled by N.
+ * Also keeps the transmission functions t_i for inelastic_map.  The returned
+ * handle owns all of it; free it with eels_smatrix_free.  Returns
+ * EELS_ERR_ARG if a probe beam lies outside the band limit, EELS_ERR_OOM if the
+ * device cannot hold n_z * n_in * (N/2)^2 * 8 bytes plus the transmissions. */
+eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* optics,
+                               void* stream, eels_smatrix** out);
+void eels_smatrix_free(eels_smatrix* sm);
+
+/* Shape of a built S-matrix: grid, slices and number of probe beams. */
+eels_status eels_smatrix_info(const eels_smatrix* sm, int* n, int* n_z, int* n_in);
+
+/* Copy the probe beam list (integer f-lattice indices p, q; k = f(p,q)/L) to host
+ * arrays of length n_in, in the column order of S_in. */
+eels_status eels_smatrix_beams(const eels_smatrix* sm, int32_t* p, int32_t* q);
+
+/* Copy S_in(depth) (complex64 [n_in][N/2][N/2], values scaled by N so that a
+ * unit-norm plane wave has unit-modulus samples) to device memory `dst`. */
+eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* dst, void* stream);
+
+/* EELS map of the linear algorithm (Sec. III second listing, realised exactly
+ * with S_out streamed backwards one depth at a time):
+ *   map[m][iy][ix] = f^2 sum_{sites s in window(R)} sum_d |sum_j M_{s,m}[d,j] a_j(R)|^2
+ * map_out is FP64 [n_types][n_sy][n_sx], caller-owned, host or device
+ * (map_on_device); it is overwritten.  beta is the EELS collection semi-angle.
+ * EELS_ERR_UNSUPPORTED if the precision is not built. */
+eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
+                               const eels_scan* scan, double beta, int precision,
+                               double* map_out, int map_on_device, void* stream);
+
+/* The conventional quadratic algorithm (Sec. III first listing) on the GPU,
+ * batched over probes and inelastic waves, same FFT kernels.  If positions is
+ * non-NULL only the n_pos scan points positions[2k] = iy, positions[2k+1] = ix
+ * (host int32) are computed and the rest of the map is zero.  Returns in
+ * *steps (if non-NULL) the number of multislice operations performed, which
+ * equals the paper's count sum_i n_states,i (n_z - i) + n_z per probe. */
+eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spec,
+                                         const eels_optics* optics, const eels_transitions* tr,
+                                         const eels_scan* scan, double beta,
+                                         const int32_t* positions, int n_pos, double* map_out,
+                                         int map_on_device, void* stream, int64_t* steps);
+
+/* Per-kernel device timing.  While enabled, every kernel launch made by calls on
+ * this context is bracketed by CUDA events recorded on the launch stream.
+ * eels_profile_read synchronises those events and writes a JSON object
+ * {"kernel": {"launches": L, "ms": T}, ...} (NUL-terminated, at most cap bytes)
+ * and returns the number of bytes the full text needs; the records are then
+ * cleared.  Disabled by default. */
+eels_status eels_profile_enable(eels_ctx* ctx, int on);
+int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
+
+/* Number of f-lattice beams with lambda |k| <= angle (Sec. III, pi alpha^2 L^2 / f^2). */
+int eels_count_beams(int n, double cell, double lambda, int f, double angle);
+
+/* The paper's memory model (Sec. III memory paragraph), in bytes of
+ * single-precision complex arrays: out[0] = conventional minimum, 4 N^2;
+ * out[1] = transmission functions, n_z N^2; out[2] = both scattering matrices,
+ * (planes_in + planes_out) (N/2)^2.  Returns EELS_ERR_ARG for invalid sizes. */
+eels_status eels_memory_model(int n, int n_z, int planes_in, int planes_out, int64_t out[3]);
+
+/* Device bytes of a request (Sec. III memory paragraph):
+ * transmissions n_z N^2 + S_in n_z n_in (N/2)^2 + one S_out depth n_out (N/2)^2
+ * complex64 values, plus two multislice work arrays of chunk * N * N/2 values.
+ * Returns -1 for invalid arguments. */
+int64_t eels_footprint_bytes(int n, int n_z, int n_in, int n_out, int chunk);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STEM_EELS_H */

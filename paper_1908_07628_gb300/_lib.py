@@ -1,0 +1,311 @@
+"""ctypes binding of libstemeels.so (include/stem_eels.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be numpy arrays (host) or torch CUDA tensors (device); the
+binding passes their pointers and the matching host/device flag.  If the shared
+object is missing or fails to load, every call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libstemeels.so")
+
+EELS_PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2}
+_STATUS = {0: "EELS_OK", 1: "EELS_ERR_ARG", 2: "EELS_ERR_UNSUPPORTED", 3: "EELS_ERR_OOM",
+           4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT"}
+
+
+class EelsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Specimen(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_z", C.c_int), ("cell", C.c_double),
+                ("vproj", C.c_void_p), ("vproj_on_device", C.c_int)]
+
+
+class Optics(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("sigma", C.c_double), ("dz", C.c_double),
+                ("f", C.c_int), ("alpha", C.c_double)]
+
+
+class Transitions(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("n_types", C.c_int), ("w", C.c_int),
+                ("H", C.c_void_p), ("slice", C.c_void_p), ("win_x0", C.c_void_p),
+                ("win_y0", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class Scan(C.Structure):
+    _fields_ = [("n_sx", C.c_int), ("n_sy", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("step_x", C.c_double), ("step_y", C.c_double)]
+
+
+EXPORTS = {
+    "eels_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "eels_destroy": (None, [C.c_void_p]),
+    "eels_last_error": (C.c_char_p, [C.c_void_p]),
+    "eels_build_smatrix": (C.c_int, [C.c_void_p, C.POINTER(Specimen), C.POINTER(Optics),
+                                     C.c_void_p, C.POINTER(C.c_void_p)]),
+    "eels_smatrix_free": (None, [C.c_void_p]),
+    "eels_smatrix_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int)]),
+    "eels_smatrix_beams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "eels_smatrix_copy_depth": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "eels_inelastic_map": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Transitions),
+                                     C.POINTER(Scan), C.c_double, C.c_int, C.c_void_p, C.c_int,
+                                     C.c_void_p]),
+    "eels_quadratic_reference_map": (C.c_int, [C.c_void_p, C.POINTER(Specimen), C.POINTER(Optics),
+                                               C.POINTER(Transitions), C.POINTER(Scan), C.c_double,
+                                               C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                               C.c_void_p, C.POINTER(C.c_int64)]),
+    "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
+    "eels_count_beams": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double]),
+    "eels_memory_model": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
+    "eels_footprint_bytes": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libstemeels.so not built ({LIB_PATH}); run "
+                               "paper_1908_07628_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_cuda_tensor(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device, keepalive) of a contiguous array of the given numpy dtype."""
+    if _is_cuda_tensor(a):
+        import torch
+        want = {np.float32: torch.float32, np.complex64: torch.complex64, np.float64: torch.float64,
+                np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"device array must be a contiguous {want} tensor")
+        return C.c_void_p(a.data_ptr()), 1, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(C.c_void_p), 0, arr
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """An eels_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        st = self._lib.eels_create(device, C.byref(h))
+        if st != 0:
+            raise EelsError(st, f"eels_create(device={device})")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.eels_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self._lib.eels_last_error(self._h)
+            raise EelsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.eels_profile_enable(self._h, 1 if on else 0), "profile_enable")
+
+    def profile_read(self) -> dict:
+        """Per-kernel {launches, ms} recorded since the last read (clears the records)."""
+        import json
+        need = self._lib.eels_profile_read(self._h, None, 0)
+        buf = C.create_string_buffer(max(need, 2))
+        self._lib.eels_profile_read(self._h, buf, len(buf))
+        return json.loads(buf.value.decode() or "{}")
+
+    # -- the three calls of the method --------------------------------------------------
+
+    def build_smatrix(self, vproj, cell, lam, sigma, dz, f, alpha, stream=None) -> "SMatrix":
+        """eels_build_smatrix: S_in at every depth for the probe aperture alpha."""
+        v, on_dev, keep = _ptr(vproj, np.float32)
+        n_z, n = int(vproj.shape[0]), int(vproj.shape[-1])
+        spec = Specimen(n, n_z, float(cell), v, on_dev)
+        op = Optics(float(lam), float(sigma), float(dz), int(f), float(alpha))
+        h = C.c_void_p()
+        st = self._lib.eels_build_smatrix(self._h, C.byref(spec), C.byref(op), _stream(stream),
+                                          C.byref(h))
+        del keep
+        self._check(st, "eels_build_smatrix")
+        return SMatrix(self, h)
+
+    def inelastic_map(self, sm, H, site_slice, win_x0, win_y0, site_x, site_y, scan, beta,
+                      precision="fp32", out=None, stream=None):
+        """eels_inelastic_map: FP64 map [n_types][n_sy][n_sx] (numpy, or into a CUDA tensor)."""
+        tr, keep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
+        sc = Scan(*[int(v) for v in scan[:2]], *[float(v) for v in scan[2:]])
+        shape = (int(H.shape[1]), int(scan[1]), int(scan[0]))
+        out_arr = np.zeros(shape) if out is None else out
+        o, o_dev, okeep = _ptr(out_arr, np.float64)
+        st = self._lib.eels_inelastic_map(self._h, sm._h, C.byref(tr), C.byref(sc), float(beta),
+                                          EELS_PREC[precision], o, o_dev, _stream(stream))
+        del keep
+        self._check(st, "eels_inelastic_map")
+        if out is None or not o_dev:
+            if o_dev == 0 and out is not None and okeep is not out:
+                out[...] = okeep
+            return okeep if out is None else out
+        return out
+
+    def quadratic_reference_map(self, vproj, cell, lam, sigma, dz, f, alpha, H, site_slice,
+                                win_x0, win_y0, site_x, site_y, scan, beta, positions=None,
+                                stream=None):
+        """eels_quadratic_reference_map: conventional algorithm on the GPU.  Returns (map, steps)."""
+        v, on_dev, vkeep = _ptr(vproj, np.float32)
+        n_z, n = int(vproj.shape[0]), int(vproj.shape[-1])
+        spec = Specimen(n, n_z, float(cell), v, on_dev)
+        op = Optics(float(lam), float(sigma), float(dz), int(f), float(alpha))
+        tr, keep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
+        sc = Scan(*[int(x) for x in scan[:2]], *[float(x) for x in scan[2:]])
+        out = np.zeros((int(H.shape[1]), int(scan[1]), int(scan[0])))
+        steps = C.c_int64(0)
+        if positions is None:
+            pp, npos, pkeep = None, 0, None
+        else:
+            pkeep = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(-1, 2))
+            pp, npos = pkeep.ctypes.data_as(C.c_void_p), int(pkeep.shape[0])
+        st = self._lib.eels_quadratic_reference_map(
+            self._h, C.byref(spec), C.byref(op), C.byref(tr), C.byref(sc), float(beta), pp, npos,
+            out.ctypes.data_as(C.c_void_p), 0, _stream(stream), C.byref(steps))
+        del keep, vkeep, pkeep
+        self._check(st, "eels_quadratic_reference_map")
+        return out, int(steps.value)
+
+
+class SMatrix:
+    """Library-owned S_in handle (eels_smatrix)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self._h = h
+        n, nz, nin = C.c_int(), C.c_int(), C.c_int()
+        ctx._check(ctx._lib.eels_smatrix_info(h, C.byref(n), C.byref(nz), C.byref(nin)), "info")
+        self.n, self.n_z, self.n_in = n.value, nz.value, nin.value
+
+    def beams(self):
+        p = np.zeros(self.n_in, dtype=np.int32)
+        q = np.zeros(self.n_in, dtype=np.int32)
+        self.ctx._check(self.ctx._lib.eels_smatrix_beams(self._h, p.ctypes.data_as(C.c_void_p),
+                                                         q.ctypes.data_as(C.c_void_p)), "beams")
+        return p, q
+
+    def copy_depth(self, depth, dst, stream=None):
+        """Copy S_in(depth) into a complex64 CUDA tensor [n_in][N/2][N/2]."""
+        ptr, on_dev, _ = _ptr(dst, np.complex64)
+        if not on_dev:
+            raise TypeError("copy_depth needs a CUDA tensor")
+        self.ctx._check(self.ctx._lib.eels_smatrix_copy_depth(self._h, int(depth), ptr,
+                                                              _stream(stream)), "copy_depth")
+        return dst
+
+    def free(self):
+        if self._h:
+            self.ctx._lib.eels_smatrix_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _transitions(H, site_slice, win_x0, win_y0, site_x, site_y):
+    h, h_dev, hk = _ptr(H, np.complex64)
+    arrs = [np.ascontiguousarray(site_slice, dtype=np.int32),
+            np.ascontiguousarray(win_x0, dtype=np.int32),
+            np.ascontiguousarray(win_y0, dtype=np.int32),
+            np.ascontiguousarray(site_x, dtype=np.float64),
+            np.ascontiguousarray(site_y, dtype=np.float64)]
+    ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
+    tr = Transitions(int(H.shape[0]), int(H.shape[1]), int(H.shape[2]), h, *ptrs, h_dev)
+    return tr, (hk, arrs)
+
+
+def count_beams(n, cell, lam, f, angle) -> int:
+    return int(load().eels_count_beams(int(n), float(cell), float(lam), int(f), float(angle)))
+
+
+def memory_model(n, n_z, planes_in, planes_out):
+    out = (C.c_int64 * 3)()
+    st = load().eels_memory_model(int(n), int(n_z), int(planes_in), int(planes_out), out)
+    if st != 0:
+        raise EelsError(st, "eels_memory_model")
+    return [int(v) for v in out]
+
+
+def footprint_bytes(n, n_z, n_in, n_out, chunk) -> int:
+    return int(load().eels_footprint_bytes(int(n), int(n_z), int(n_in), int(n_out), int(chunk)))
+
+
+# -- convenience: unpack any object carrying the workload attributes ------------------------
+
+def build_smatrix_for(ctx: Context, wl, vproj=None, stream=None) -> SMatrix:
+    return ctx.build_smatrix(wl.vproj if vproj is None else vproj, wl.cell, wl.lam, wl.sigma,
+                             wl.dz, wl.f, wl.alpha, stream=stream)
+
+
+def inelastic_map_for(ctx: Context, sm: SMatrix, wl, precision="fp32", H=None, out=None,
+                      stream=None):
+    return ctx.inelastic_map(sm, wl.H if H is None else H, wl.site_slice, wl.win_x0, wl.win_y0,
+                             wl.site_x, wl.site_y, wl.scan, wl.beta, precision=precision, out=out,
+                             stream=stream)
+
+
+def quadratic_reference_map_for(ctx: Context, wl, positions=None, stream=None):
+    return ctx.quadratic_reference_map(wl.vproj, wl.cell, wl.lam, wl.sigma, wl.dz, wl.f, wl.alpha,
+                                       wl.H, wl.site_slice, wl.win_x0, wl.win_y0, wl.site_x,
+                                       wl.site_y, wl.scan, wl.beta, positions=positions,
+                                       stream=stream)

@@ -1,0 +1,740 @@
+// Host side of the C ABI declared in include/stem_eels.h: argument checks, beam
+// lists, PRISM window lists, device buffers and the launch order of the kernels.
+// Compiled with -ffp-contract=off so that the FP64 decisions taken here (beam
+// inside an aperture, site inside a probe's PRISM window) are the plain IEEE
+// sequence of operations the definitions state.
+#include "stem_eels.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct eels_ctx {
+  int device = 0;
+  std::string err;
+  std::map<int, float2*> tw;   // device twiddle table exp(-2 pi i k/N), by N
+  // kernel timing records (eels_profile_enable)
+  bool profiling = false;
+  struct Rec { const char* name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> spare;
+};
+
+struct eels_smatrix {
+  eels_ctx* ctx = nullptr;
+  int n = 0, n_z = 0, f = 1;
+  double cell = 0, lam = 0, sigma = 0, dz = 0, alpha = 0;
+  std::vector<int> bp, bq;     // probe beams, f-lattice integer indices
+  float2* t = nullptr;         // [n_z][n][n]
+  float2* ptab = nullptr;      // [n/2][n/2] box order, forward propagator / N^2
+  float2* s_in = nullptr;      // [n_z][n_in][n/2][n/2]
+};
+
+namespace {
+
+using eels::launch_col_pass;
+using eels::launch_row_pass;
+
+constexpr double kPi = 3.14159265358979323846;
+
+eels_status fail(eels_ctx* ctx, eels_status code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+eels_status cuda_fail(eels_ctx* ctx, cudaError_t e, const char* where) {
+  const eels_status code = (e == cudaErrorMemoryAllocation) ? EELS_ERR_OOM : EELS_ERR_CUDA;
+  return fail(ctx, code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Brackets one kernel launch with events when the context is profiling.
+struct Prof {
+  eels_ctx* ctx;
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Prof(eels_ctx* c, const char* n, cudaStream_t s) : ctx(c), name(n), st(s) {
+    if (ctx->profiling) { a = get(); cudaEventRecord(a, st); }
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEvent_t b = get();
+    cudaEventRecord(b, st);
+    ctx->recs.push_back({name, a, b});
+  }
+  cudaEvent_t get() {
+    if (!ctx->spare.empty()) { cudaEvent_t e = ctx->spare.back(); ctx->spare.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+#define EELS_CK(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+  } while (0)
+
+// Stream-ordered device buffer freed at scope exit.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { if (p) cudaFreeAsync(p, s); }
+  cudaError_t alloc(size_t count, cudaStream_t st) {
+    s = st;
+    if (count == 0) count = 1;
+    return cudaMallocAsync((void**)&p, count * sizeof(T), st);
+  }
+  cudaError_t upload(const T* host, size_t count, cudaStream_t st) {
+    cudaError_t e = alloc(count, st);
+    if (e != cudaSuccess || count == 0) return e;
+    return cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, st);
+  }
+};
+
+// f-lattice beams (p, q), k = f(p, q)/L, with lambda |k| <= angle (Sec. III).
+void lattice_beams(int n, double cell, double lam, int f, double angle, std::vector<int>& p,
+                   std::vector<int>& q) {
+  p.clear();
+  q.clear();
+  const int pmax = (int)std::ceil(angle * cell / (lam * f)) + 1;
+  for (int b = -pmax; b <= pmax; ++b)
+    for (int a = -pmax; a <= pmax; ++a)
+      if (lam * f * std::sqrt((double)(a * a + b * b)) / cell <= angle) {
+        p.push_back(a);
+        q.push_back(b);
+      }
+  (void)n;
+}
+
+bool inside_band(int n, int f, const std::vector<int>& p, const std::vector<int>& q) {
+  for (size_t i = 0; i < p.size(); ++i) {
+    const int64_t k2 = (int64_t)f * f * ((int64_t)p[i] * p[i] + (int64_t)q[i] * q[i]);
+    if (16 * k2 >= (int64_t)n * n) return false;
+  }
+  return true;
+}
+
+// PRISM window along one axis: minimum-image s - r in [-L/(2f), L/(2f)).
+bool axis_in_window(double s, double r, double cell, int f) {
+  double d = s - r;
+  d = d - cell * std::floor(d / cell + 0.5);
+  const double h = cell / (2 * f);
+  return d >= -h && d < h;
+}
+
+eels_status twiddles(eels_ctx* ctx, int n, float2** out) {
+  auto it = ctx->tw.find(n);
+  if (it != ctx->tw.end()) {
+    *out = it->second;
+    return EELS_OK;
+  }
+  std::vector<float2> h(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * kPi * (double)k / (double)n;
+    h[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  float2* d = nullptr;
+  EELS_CK(cudaMalloc((void**)&d, n * sizeof(float2)));
+  EELS_CK(cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  ctx->tw[n] = d;
+  *out = d;
+  return EELS_OK;
+}
+
+eels_status check_specimen(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* op) {
+  if (!spec || !op || !spec->vproj) return fail(ctx, EELS_ERR_ARG, "null specimen/optics");
+  if (spec->n_z <= 0 || !(spec->cell > 0)) return fail(ctx, EELS_ERR_ARG, "bad n_z or cell");
+  if (!eels::grid_supported(spec->n))
+    return fail(ctx, EELS_ERR_UNSUPPORTED, "grid size " + std::to_string(spec->n) + " not built");
+  if (op->f < 1 || !(op->lambda > 0) || !(op->dz > 0) || !(op->alpha > 0))
+    return fail(ctx, EELS_ERR_ARG, "bad optics");
+  return EELS_OK;
+}
+
+// Transmission functions t_i and the forward propagator table for a specimen.
+eels_status build_slices(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* op,
+                         cudaStream_t st, float2* t, float2* ptab) {
+  const int n = spec->n;
+  const int64_t count = (int64_t)spec->n_z * n * n;
+  const float* v = spec->vproj;
+  DevBuf<float> vtmp;
+  if (!spec->vproj_on_device) {
+    EELS_CK(vtmp.upload(spec->vproj, (size_t)count, st));
+    v = vtmp.p;
+  }
+  { Prof pr(ctx, "transmission", st); EELS_CK(eels::launch_transmission(v, op->sigma, t, count, st)); }
+  EELS_CK(eels::launch_propagator_table(ptab, n, spec->cell, op->lambda, op->dz,
+                                        (float)(1.0 / ((double)n * n)), st));
+  return EELS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eels_status eels_create(int device, eels_ctx** out) {
+  if (!out) return EELS_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return EELS_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return EELS_ERR_CUDA;
+  eels_ctx* c = new eels_ctx();
+  c->device = device;
+  // keep freed stream-ordered allocations cached between calls
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = c;
+  return EELS_OK;
+}
+
+void eels_destroy(eels_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  for (auto& kv : ctx->tw) cudaFree(kv.second);
+  for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->spare) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* eels_last_error(const eels_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+eels_status eels_profile_enable(eels_ctx* ctx, int on) {
+  if (!ctx) return EELS_ERR_ARG;
+  ctx->profiling = on != 0;
+  return EELS_OK;
+}
+
+int eels_profile_read(eels_ctx* ctx, char* buf, int cap) {
+  if (!ctx) return -1;
+  cudaSetDevice(ctx->device);
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  for (auto& r : ctx->recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& e = agg[r.name];
+    e.first += 1;
+    e.second += ms;
+    ctx->spare.push_back(r.a);
+    ctx->spare.push_back(r.b);
+  }
+  ctx->recs.clear();
+  std::string out = "{";
+  for (auto& kv : agg) {
+    char tmp[256];
+    std::snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}",
+                  out.size() > 1 ? ", " : "", kv.first.c_str(), (long long)kv.second.first,
+                  kv.second.second);
+    out += tmp;
+  }
+  out += "}";
+  if (buf && cap > 0) {
+    std::strncpy(buf, out.c_str(), (size_t)cap - 1);
+    buf[cap - 1] = 0;
+  }
+  return (int)out.size() + 1;
+}
+
+int eels_count_beams(int n, double cell, double lambda, int f, double angle) {
+  if (f < 1 || !(cell > 0) || !(lambda > 0) || angle < 0) return -1;
+  std::vector<int> p, q;
+  lattice_beams(n, cell, lambda, f, angle, p, q);
+  return (int)p.size();
+}
+
+eels_status eels_memory_model(int n, int n_z, int planes_in, int planes_out, int64_t out[3]) {
+  if (!out || n <= 0 || n % 2 || n_z < 0 || planes_in < 0 || planes_out < 0) return EELS_ERR_ARG;
+  const int64_t c = 8;   // bytes of a single-precision complex value
+  out[0] = 4 * c * (int64_t)n * n;
+  out[1] = c * (int64_t)n_z * n * n;
+  out[2] = c * (int64_t)(planes_in + planes_out) * (n / 2) * (n / 2);
+  return EELS_OK;
+}
+
+int64_t eels_footprint_bytes(int n, int n_z, int n_in, int n_out, int chunk) {
+  int64_t mm[3];
+  if (eels_memory_model(n, n_z, 0, 0, mm) != EELS_OK || n_in < 0 || n_out < 0 || chunk < 0)
+    return -1;
+  const int64_t plane = 8 * (int64_t)(n / 2) * (n / 2);
+  return mm[1] + plane * ((int64_t)n_z * n_in + n_out) + 2 * 8 * (int64_t)chunk * n * (n / 2);
+}
+
+eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* op,
+                               void* stream, eels_smatrix** out) {
+  if (!ctx || !out) return EELS_ERR_ARG;
+  *out = nullptr;
+  eels_status r = check_specimen(ctx, spec, op);
+  if (r != EELS_OK) return r;
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = spec->n, nh = n / 2, n_z = spec->n_z;
+  std::vector<int> bp, bq;
+  lattice_beams(n, spec->cell, op->lambda, op->f, op->alpha, bp, bq);
+  if (bp.empty()) return fail(ctx, EELS_ERR_ARG, "no probe beam inside the aperture");
+  if (!inside_band(n, op->f, bp, bq))
+    return fail(ctx, EELS_ERR_ARG, "probe aperture extends beyond the band limit");
+  const int n_in = (int)bp.size();
+  float2* tw = nullptr;
+  if ((r = twiddles(ctx, n, &tw)) != EELS_OK) return r;
+
+  eels_smatrix* sm = new eels_smatrix();
+  sm->ctx = ctx;
+  sm->n = n; sm->n_z = n_z; sm->f = op->f;
+  sm->cell = spec->cell; sm->lam = op->lambda; sm->sigma = op->sigma; sm->dz = op->dz;
+  sm->alpha = op->alpha;
+  sm->bp = bp; sm->bq = bq;
+  auto bail = [&](eels_status code) { eels_smatrix_free(sm); return code; };
+  const int64_t plane = (int64_t)nh * nh;
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&sm->t, sizeof(float2) * (size_t)n_z * n * n)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&sm->ptab, sizeof(float2) * (size_t)plane)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&sm->s_in, sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane))) !=
+          cudaSuccess)
+    return bail(cuda_fail(ctx, e, "S-matrix allocation"));
+  if ((r = build_slices(ctx, spec, op, st, sm->t, sm->ptab)) != EELS_OK) return bail(r);
+
+  std::vector<int> px(n_in), py(n_in);
+  std::vector<float2> amp(n_in, make_float2(1.f, 0.f));
+  for (int j = 0; j < n_in; ++j) { px[j] = op->f * bp[j]; py[j] = op->f * bq[j]; }
+  DevBuf<int> dpx, dpy;
+  DevBuf<float2> damp, W, Phi;
+  if ((e = dpx.upload(px.data(), n_in, st)) != cudaSuccess ||
+      (e = dpy.upload(py.data(), n_in, st)) != cudaSuccess ||
+      (e = damp.upload(amp.data(), n_in, st)) != cudaSuccess ||
+      (e = W.alloc((size_t)n_in * n * nh, st)) != cudaSuccess ||
+      (e = Phi.alloc((size_t)n_in * n * nh, st)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "S_in work buffers"));
+  {
+    Prof pr(ctx, "init_plane_waves", st);
+    if ((e = eels::launch_init_plane_waves(W.p, n, n_in, dpx.p, dpy.p, damp.p, tw, st)) != cudaSuccess)
+      return bail(cuda_fail(ctx, e, "init plane waves"));
+  }
+  for (int i = 0; i < n_z; ++i) {
+    const bool last = (i == n_z - 1);
+    {
+      Prof pr(ctx, "row_pass", st);
+      e = launch_row_pass(n, n_in, W.p, Phi.p, sm->t + (int64_t)i * n * n, 0, 1,
+                          sm->s_in + (int64_t)i * n_in * plane, n_in, plane, last ? 0 : 1, tw, st);
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "row pass"));
+    if (!last) {
+      Prof pr(ctx, "col_pass", st);
+      e = launch_col_pass(n, n_in, Phi.p, W.p, sm->ptab, 0, 0, nullptr, nullptr, nullptr, 0.0, tw,
+                          st);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "column pass"));
+    }
+  }
+  *out = sm;
+  return EELS_OK;
+}
+
+void eels_smatrix_free(eels_smatrix* sm) {
+  if (!sm) return;
+  cudaSetDevice(sm->ctx->device);
+  cudaFree(sm->t);
+  cudaFree(sm->ptab);
+  cudaFree(sm->s_in);
+  delete sm;
+}
+
+eels_status eels_smatrix_info(const eels_smatrix* sm, int* n, int* n_z, int* n_in) {
+  if (!sm) return EELS_ERR_ARG;
+  if (n) *n = sm->n;
+  if (n_z) *n_z = sm->n_z;
+  if (n_in) *n_in = (int)sm->bp.size();
+  return EELS_OK;
+}
+
+eels_status eels_smatrix_beams(const eels_smatrix* sm, int32_t* p, int32_t* q) {
+  if (!sm || !p || !q) return EELS_ERR_ARG;
+  for (size_t j = 0; j < sm->bp.size(); ++j) { p[j] = sm->bp[j]; q[j] = sm->bq[j]; }
+  return EELS_OK;
+}
+
+eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* dst, void* stream) {
+  if (!sm || !dst || depth < 0 || depth >= sm->n_z) return EELS_ERR_ARG;
+  eels_ctx* ctx = sm->ctx;
+  EELS_CK(cudaSetDevice(ctx->device));
+  const int64_t per = (int64_t)sm->bp.size() * (sm->n / 2) * (sm->n / 2);
+  EELS_CK(cudaMemcpyAsync(dst, sm->s_in + depth * per, per * sizeof(float2),
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return EELS_OK;
+}
+
+namespace {
+
+struct SiteLists {
+  std::vector<int> xoff, xcnt, xlist, yoff, ycnt, ylist;
+  int max_nr = 0;
+};
+
+SiteLists window_lists(const eels_transitions* tr, const eels_scan* sc, double cell, int f) {
+  SiteLists L;
+  const int S = tr->n_sites;
+  L.xoff.resize(S); L.xcnt.resize(S); L.yoff.resize(S); L.ycnt.resize(S);
+  for (int s = 0; s < S; ++s) {
+    L.xoff[s] = (int)L.xlist.size();
+    for (int ix = 0; ix < sc->n_sx; ++ix)
+      if (axis_in_window(tr->x[s], sc->x0 + (double)ix * sc->step_x, cell, f)) L.xlist.push_back(ix);
+    L.xcnt[s] = (int)L.xlist.size() - L.xoff[s];
+    L.yoff[s] = (int)L.ylist.size();
+    for (int iy = 0; iy < sc->n_sy; ++iy)
+      if (axis_in_window(tr->y[s], sc->y0 + (double)iy * sc->step_y, cell, f)) L.ylist.push_back(iy);
+    L.ycnt[s] = (int)L.ylist.size() - L.yoff[s];
+    L.max_nr = std::max(L.max_nr, L.xcnt[s] * L.ycnt[s]);
+  }
+  return L;
+}
+
+eels_status check_transitions(eels_ctx* ctx, const eels_transitions* tr, const eels_scan* sc,
+                              int n, int n_z) {
+  if (!tr || !sc) return fail(ctx, EELS_ERR_ARG, "null transitions/scan");
+  if (tr->n_sites < 0 || tr->n_types <= 0 || tr->w < 1 || tr->w > n / 2)
+    return fail(ctx, EELS_ERR_ARG, "bad transition sizes (need 1 <= w <= N/2)");
+  if (tr->n_sites > 0 &&
+      (!tr->H || !tr->slice || !tr->win_x0 || !tr->win_y0 || !tr->x || !tr->y))
+    return fail(ctx, EELS_ERR_ARG, "null transition array");
+  for (int s = 0; s < tr->n_sites; ++s) {
+    if (tr->slice[s] < 0 || tr->slice[s] >= n_z) return fail(ctx, EELS_ERR_ARG, "site slice out of range");
+    if (tr->win_x0[s] < 0 || tr->win_x0[s] >= n / 2 || tr->win_y0[s] < 0 || tr->win_y0[s] >= n / 2)
+      return fail(ctx, EELS_ERR_ARG, "window origin outside the N/2 grid");
+  }
+  if (sc->n_sx <= 0 || sc->n_sy <= 0) return fail(ctx, EELS_ERR_ARG, "empty scan");
+  return EELS_OK;
+}
+
+}  // namespace
+
+eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
+                               const eels_scan* sc, double beta, int precision, double* map_out,
+                               int map_on_device, void* stream) {
+  if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
+  eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
+  if (r != EELS_OK) return r;
+  if (precision != EELS_PREC_FP32)
+    return fail(ctx, EELS_ERR_UNSUPPORTED, "precision not built");
+  if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = sm->n, nh = n / 2, n_z = sm->n_z, f = sm->f;
+  const int n_in = (int)sm->bp.size();
+  const int T = tr->n_types, w = tr->w, S = tr->n_sites;
+  const int64_t plane = (int64_t)nh * nh;
+  const int64_t n_map = (int64_t)T * sc->n_sx * sc->n_sy;
+
+  std::vector<int> dp, dq;
+  lattice_beams(n, sm->cell, sm->lam, f, beta, dp, dq);
+  if (dp.empty()) return fail(ctx, EELS_ERR_ARG, "no detector beam inside beta");
+  if (!inside_band(n, f, dp, dq))
+    return fail(ctx, EELS_ERR_ARG, "detector aperture extends beyond the band limit");
+  const int n_out = (int)dp.size();
+  float2* tw = nullptr;
+  if ((r = twiddles(ctx, n, &tw)) != EELS_OK) return r;
+
+  // PRISM windows and the transitions of each slice (sites reached by some probe)
+  SiteLists L = window_lists(tr, sc, sm->cell, f);
+  std::vector<std::vector<int>> tr_site(n_z), tr_type(n_z);
+  for (int s = 0; s < S; ++s) {
+    if (L.xcnt[s] == 0 || L.ycnt[s] == 0) continue;
+    for (int m = 0; m < T; ++m) {
+      tr_site[tr->slice[s]].push_back(s);
+      tr_type[tr->slice[s]].push_back(m);
+    }
+  }
+
+  DevBuf<float2> dH, Sout, W, Phi, M, ax, ay, damp;
+  DevBuf<int> dwx, dwy, dxoff, dxcnt, dxlist, dyoff, dycnt, dylist, dpx, dpy, dbp, dbq, dts, dtt;
+  DevBuf<double> dmap;
+  const float2* H = (const float2*)tr->H;
+  const size_t hcount = (size_t)S * T * w * w;
+  if (!tr->on_device) {
+    EELS_CK(dH.upload((const float2*)tr->H, hcount, st));
+    H = dH.p;
+  }
+  EELS_CK(dwx.upload(tr->win_x0, S, st));
+  EELS_CK(dwy.upload(tr->win_y0, S, st));
+  EELS_CK(dxoff.upload(L.xoff.data(), S, st));
+  EELS_CK(dxcnt.upload(L.xcnt.data(), S, st));
+  EELS_CK(dxlist.upload(L.xlist.data(), L.xlist.size(), st));
+  EELS_CK(dyoff.upload(L.yoff.data(), S, st));
+  EELS_CK(dycnt.upload(L.ycnt.data(), S, st));
+  EELS_CK(dylist.upload(L.ylist.data(), L.ylist.size(), st));
+  EELS_CK(dbp.upload(sm->bp.data(), n_in, st));
+  EELS_CK(dbq.upload(sm->bq.data(), n_in, st));
+  EELS_CK(ax.alloc((size_t)n_in * sc->n_sx, st));
+  EELS_CK(ay.alloc((size_t)n_in * sc->n_sy, st));
+  EELS_CK(eels::launch_phase_table(ax.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x, sc->n_sx, st));
+  EELS_CK(eels::launch_phase_table(ay.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y, sc->n_sy, st));
+
+  // flattened transition lists of all slices
+  std::vector<int> all_site, all_type, slice_off(n_z + 1, 0);
+  for (int i = 0; i < n_z; ++i) {
+    slice_off[i] = (int)all_site.size();
+    all_site.insert(all_site.end(), tr_site[i].begin(), tr_site[i].end());
+    all_type.insert(all_type.end(), tr_type[i].begin(), tr_type[i].end());
+  }
+  slice_off[n_z] = (int)all_site.size();
+  EELS_CK(dts.upload(all_site.data(), all_site.size(), st));
+  EELS_CK(dtt.upload(all_type.data(), all_type.size(), st));
+
+  // detector plane waves at the exit surface, carried back by conj(P) first:
+  // beta_d(n_z - 1) = conj(P(k_d)) |k_d>
+  std::vector<int> px(n_out), py(n_out);
+  std::vector<float2> amp(n_out);
+  for (int d = 0; d < n_out; ++d) {
+    px[d] = f * dp[d];
+    py[d] = f * dq[d];
+    double a = sm->lam * sm->dz * (double)((int64_t)px[d] * px[d] + (int64_t)py[d] * py[d]) /
+               (sm->cell * sm->cell);
+    a -= 2.0 * std::floor(0.5 * a);
+    amp[d] = make_float2((float)std::cos(kPi * a), (float)std::sin(kPi * a));
+  }
+  EELS_CK(dpx.upload(px.data(), n_out, st));
+  EELS_CK(dpy.upload(py.data(), n_out, st));
+  EELS_CK(damp.upload(amp.data(), n_out, st));
+  EELS_CK(Sout.alloc((size_t)n_out * plane, st));
+  EELS_CK(W.alloc((size_t)n_out * n * nh, st));
+  EELS_CK(Phi.alloc((size_t)n_out * n * nh, st));
+  EELS_CK(dmap.alloc((size_t)n_map, st));
+  EELS_CK(cudaMemsetAsync(dmap.p, 0, sizeof(double) * n_map, st));
+
+  // M buffer: a batch of transitions, at most ~1 GiB
+  const int64_t m_stride = (int64_t)n_out * n_in;
+  int max_tr = 0;
+  for (int i = 0; i < n_z; ++i) max_tr = std::max(max_tr, (int)tr_site[i].size());
+  const int batch = (int)std::max<int64_t>(1, std::min<int64_t>(
+      std::max(max_tr, 1), (int64_t)(1 << 30) / (m_stride * (int64_t)sizeof(float2))));
+  EELS_CK(M.alloc((size_t)batch * m_stride, st));
+
+  {
+    Prof pr(ctx, "init_plane_waves", st);
+    EELS_CK(eels::launch_init_plane_waves(W.p, n, n_out, dpx.p, dpy.p, damp.p, tw, st));
+  }
+  eels::WindowLists wl{dxoff.p, dxcnt.p, dxlist.p, dyoff.p, dycnt.p, dylist.p, L.max_nr};
+  for (int i = n_z - 1; i >= 0; --i) {
+    // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
+    {
+      Prof pr(ctx, "row_pass_adjoint", st);
+      EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, sm->t + (int64_t)i * n * n, 1, 2, Sout.p, n_out,
+                              plane, i > 0 ? 1 : 0, tw, st));
+    }
+    const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
+    for (int b0 = slice_off[i]; b0 < slice_off[i + 1]; b0 += batch) {
+      eels::TransitionBatch tb{dts.p + b0, dtt.p + b0, std::min(batch, slice_off[i + 1] - b0)};
+      {
+        Prof pr(ctx, "gemm1_fp32", st);
+        EELS_CK(eels::launch_gemm1_fp32(Sout.p, Sin, nh, n_out, n_in, w, H, T, tb, dwx.p, dwy.p,
+                                        M.p, m_stride, st));
+      }
+      {
+        Prof pr(ctx, "gemm2_abs2_fp32", st);
+        EELS_CK(eels::launch_gemm2_abs2_fp32(M.p, m_stride, n_out, n_in, ax.p, ay.p, sc->n_sx,
+                                             sc->n_sy, tb, wl, dmap.p, st));
+      }
+    }
+    if (i > 0) {
+      Prof pr(ctx, "col_pass_adjoint", st);
+      EELS_CK(launch_col_pass(n, n_out, Phi.p, W.p, sm->ptab, 1, 0, nullptr, nullptr, nullptr, 0.0,
+                              tw, st));
+    }
+  }
+  // I = f^2 (f^2/n_in) (4/N^2)^2 sum |M_gpu a_gpu|^2: S-matrices are stored scaled
+  // by N, S_out carries the factor 4 of the half-grid inner product, and the probe
+  // coefficients carry c = f/sqrt(n_in).
+  const double nn = (double)n * (double)n;
+  const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
+  EELS_CK(eels::launch_scale(dmap.p, n_map, scale, st));
+  if (map_on_device) {
+    EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
+  } else {
+    EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToHost, st));
+    EELS_CK(cudaStreamSynchronize(st));
+  }
+  return EELS_OK;
+}
+
+eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spec,
+                                         const eels_optics* op, const eels_transitions* tr,
+                                         const eels_scan* sc, double beta,
+                                         const int32_t* positions, int n_pos, double* map_out,
+                                         int map_on_device, void* stream, int64_t* steps) {
+  if (!ctx || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
+  eels_status r = check_specimen(ctx, spec, op);
+  if (r != EELS_OK) return r;
+  if ((r = check_transitions(ctx, tr, sc, spec->n, spec->n_z)) != EELS_OK) return r;
+  if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = spec->n, nh = n / 2, n_z = spec->n_z, f = op->f;
+  const int T = tr->n_types, w = tr->w, S = tr->n_sites;
+  const int64_t plane = (int64_t)nh * nh;
+  const int n_scan = sc->n_sx * sc->n_sy;
+  const int64_t n_map = (int64_t)T * n_scan;
+
+  std::vector<int> bp, bq, dp, dq;
+  lattice_beams(n, spec->cell, op->lambda, f, op->alpha, bp, bq);
+  lattice_beams(n, spec->cell, op->lambda, f, beta, dp, dq);
+  if (bp.empty() || dp.empty()) return fail(ctx, EELS_ERR_ARG, "empty aperture");
+  if (!inside_band(n, f, bp, bq) || !inside_band(n, f, dp, dq))
+    return fail(ctx, EELS_ERR_ARG, "aperture extends beyond the band limit");
+  float2* tw = nullptr;
+  if ((r = twiddles(ctx, n, &tw)) != EELS_OK) return r;
+
+  std::vector<std::pair<int, int>> pos;
+  if (positions) {
+    if (n_pos < 0) return fail(ctx, EELS_ERR_ARG, "bad n_pos");
+    for (int k = 0; k < n_pos; ++k) {
+      const int iy = positions[2 * k], ix = positions[2 * k + 1];
+      if (iy < 0 || iy >= sc->n_sy || ix < 0 || ix >= sc->n_sx)
+        return fail(ctx, EELS_ERR_ARG, "scan position out of range");
+      pos.emplace_back(iy, ix);
+    }
+  } else {
+    for (int iy = 0; iy < sc->n_sy; ++iy)
+      for (int ix = 0; ix < sc->n_sx; ++ix) pos.emplace_back(iy, ix);
+  }
+
+  DevBuf<float2> t, ptab, dH;
+  EELS_CK(t.alloc((size_t)n_z * n * n, st));
+  EELS_CK(ptab.alloc((size_t)plane, st));
+  if ((r = build_slices(ctx, spec, op, st, t.p, ptab.p)) != EELS_OK) return r;
+  const float2* H = (const float2*)tr->H;
+  if (!tr->on_device) {
+    EELS_CK(dH.upload((const float2*)tr->H, (size_t)S * T * w * w, st));
+    H = dH.p;
+  }
+  DevBuf<int> dwx, dwy, dbp, dbq;
+  EELS_CK(dwx.upload(tr->win_x0, S, st));
+  EELS_CK(dwy.upload(tr->win_y0, S, st));
+  EELS_CK(dbp.upload(bp.data(), bp.size(), st));
+  EELS_CK(dbq.upload(bq.data(), bq.size(), st));
+  // detector bins in box order [kx'][ky']
+  std::vector<uint8_t> mask((size_t)plane, 0);
+  for (size_t d = 0; d < dp.size(); ++d) {
+    int kx = f * dp[d], ky = f * dq[d];
+    kx = kx >= 0 ? kx : kx + nh;
+    ky = ky >= 0 ? ky : ky + nh;
+    mask[(size_t)kx * nh + ky] = 1;
+  }
+  DevBuf<uint8_t> dmask;
+  EELS_CK(dmask.upload(mask.data(), mask.size(), st));
+  DevBuf<double> dmap;
+  EELS_CK(dmap.alloc((size_t)n_map, st));
+  EELS_CK(cudaMemsetAsync(dmap.p, 0, sizeof(double) * n_map, st));
+
+  // transitions each probe sees, per slice
+  std::vector<std::vector<int>> by_slice(n_z);
+  for (int s = 0; s < S; ++s) by_slice[tr->slice[s]].push_back(s);
+  auto sees = [&](int s, int iy, int ix) {
+    return axis_in_window(tr->x[s], sc->x0 + (double)ix * sc->step_x, spec->cell, f) &&
+           axis_in_window(tr->y[s], sc->y0 + (double)iy * sc->step_y, spec->cell, f);
+  };
+  std::vector<int> waves_of(pos.size(), 1);
+  int64_t total_steps = 0;
+  for (size_t k = 0; k < pos.size(); ++k) {
+    for (int i = 0; i < n_z; ++i)
+      for (int s : by_slice[i])
+        if (sees(s, pos[k].first, pos[k].second)) {
+          waves_of[k] += T;
+          total_steps += (int64_t)T * (n_z - i);
+        }
+    total_steps += n_z;
+  }
+  // probe batches: at most 65535 waves and about 32 GiB of work arrays
+  const int64_t wave_bytes = 2 * (int64_t)n * nh * sizeof(float2);
+  const int64_t max_waves = std::min<int64_t>(65535, ((int64_t)32 << 30) / wave_bytes);
+  size_t k0 = 0;
+  const double c = (double)f / std::sqrt((double)bp.size());
+  while (k0 < pos.size()) {
+    size_t k1 = k0;
+    int64_t nw = 0;
+    while (k1 < pos.size() && (k1 == k0 || nw + waves_of[k1] <= max_waves)) nw += waves_of[k1++];
+    if (nw > 65535) return fail(ctx, EELS_ERR_UNSUPPORTED, "too many inelastic waves for one probe");
+    const int B = (int)(k1 - k0);
+    std::vector<double> rx(B), ry(B);
+    for (int b = 0; b < B; ++b) {
+      rx[b] = sc->x0 + (double)pos[k0 + b].second * sc->step_x;
+      ry[b] = sc->y0 + (double)pos[k0 + b].first * sc->step_y;
+    }
+    // spawn lists per slice and the map index of every wave
+    std::vector<int> wave_out((size_t)nw, -1), sp_src, sp_site, sp_type, sp_off(n_z + 1, 0);
+    int next = B;
+    for (int i = 0; i < n_z; ++i) {
+      sp_off[i] = (int)sp_src.size();
+      for (int b = 0; b < B; ++b)
+        for (int s : by_slice[i])
+          if (sees(s, pos[k0 + b].first, pos[k0 + b].second))
+            for (int m = 0; m < T; ++m) {
+              sp_src.push_back(b);
+              sp_site.push_back(s);
+              sp_type.push_back(m);
+              wave_out[next++] = m * n_scan + pos[k0 + b].first * sc->n_sx + pos[k0 + b].second;
+            }
+    }
+    sp_off[n_z] = (int)sp_src.size();
+    DevBuf<double> drx, dry;
+    DevBuf<int> dwo, dsrc, dsite, dtype;
+    DevBuf<float2> W, Phi, D;
+    EELS_CK(drx.upload(rx.data(), B, st));
+    EELS_CK(dry.upload(ry.data(), B, st));
+    EELS_CK(dwo.upload(wave_out.data(), wave_out.size(), st));
+    EELS_CK(dsrc.upload(sp_src.data(), sp_src.size(), st));
+    EELS_CK(dsite.upload(sp_site.data(), sp_site.size(), st));
+    EELS_CK(dtype.upload(sp_type.data(), sp_type.size(), st));
+    EELS_CK(W.alloc((size_t)nw * n * nh, st));
+    EELS_CK(Phi.alloc((size_t)nw * n * nh, st));
+    EELS_CK(D.alloc((size_t)B * plane, st));
+    EELS_CK(eels::launch_probe_init(W.p, n, B, drx.p, dry.p, dbp.p, dbq.p, (int)bp.size(), f,
+                                    spec->cell, c, tw, st));
+    int active = B;
+    for (int i = 0; i < n_z; ++i) {
+      {
+        Prof pr(ctx, "row_pass", st);
+        EELS_CK(launch_row_pass(n, active, W.p, Phi.p, t.p + (int64_t)i * n * n, 0, 1, D.p, B,
+                                plane, 1, tw, st));
+      }
+      eels::SpawnList sl{dsrc.p + sp_off[i], dsite.p + sp_off[i], dtype.p + sp_off[i],
+                         sp_off[i + 1] - sp_off[i], active};
+      {
+        Prof pr(ctx, "spawn", st);
+        EELS_CK(eels::launch_spawn(n, sl, D.p, H, T, w, dwx.p, dwy.p, Phi.p, tw, st));
+      }
+      active += sl.count;
+      const bool last = (i == n_z - 1);
+      {
+        Prof pr(ctx, last ? "col_pass_detect" : "col_pass", st);
+        EELS_CK(launch_col_pass(n, active, Phi.p, W.p, ptab.p, 0, last ? 1 : 0, dmask.p, dwo.p,
+                                dmap.p, (double)f * f, tw, st));
+      }
+    }
+    k0 = k1;
+  }
+  if (steps) *steps = total_steps;
+  if (map_on_device) {
+    EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
+  } else {
+    EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToHost, st));
+    EELS_CK(cudaStreamSynchronize(st));
+  }
+  return EELS_OK;
+}
+
+}  // extern "C"

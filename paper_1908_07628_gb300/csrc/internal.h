@@ -1,0 +1,84 @@
+// Internal launchers shared between the host orchestration (api.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eels {
+
+// True if the multislice kernels are compiled for grid side n.
+bool grid_supported(int n);
+
+// t[i][y][x] = exp(i sigma v[i][y][x]) with the phase in FP64 (Eqs. 3-4).
+cudaError_t launch_transmission(const float* v, double sigma, float2* t, int64_t count,
+                                cudaStream_t s);
+
+// Ptab[kx'][ky'] = B(k) exp(-i pi lambda dz |k|^2) * scale on the N/2 x N/2 box
+// (box order: index i < N/4 is frequency i, else i - N/2).  Phase argument in FP64.
+cudaError_t launch_propagator_table(float2* ptab, int n, double cell, double lam, double dz,
+                                    float scale, cudaStream_t s);
+
+// W[b][y][kx'] = amp[b] exp(2 pi i py[b] y / N) at kx' = box(px[b]), zero elsewhere:
+// the row-spectrum form of the plane wave amp * exp(2 pi i (px x + py y)/N) / N.
+cudaError_t launch_init_plane_waves(float2* W, int n, int n_waves, const int* px, const int* py,
+                                    const float2* amp, const float2* tw, cudaStream_t s);
+
+// Row pass of one slice step for n_waves waves (see multislice.cu).
+//   store_mode 0: none; 1: store Dec(t psi) (S_in); 2: store Dec(psi) before the
+//   transmission (S_out).  Only waves < s_waves are stored, at S + wave*s_stride.
+cudaError_t launch_row_pass(int n, int n_waves, const float2* W, float2* Phi, const float2* t_slice,
+                            int conj_t, int store_mode, float2* S, int s_waves, int64_t s_stride,
+                            int fft_out, const float2* tw, cudaStream_t s);
+
+// Column pass: FFT_y, crop to the band box, multiply by Ptab (or conj), and then
+//   mode 0: zero-pad and inverse FFT_y back into W;
+//   mode 1: accumulate det_scale * sum |.|^2 over det_mask bins into det_acc[wave_out[w]].
+cudaError_t launch_col_pass(int n, int n_waves, const float2* Phi, float2* W, const float2* ptab,
+                            int conj_p, int mode, const uint8_t* det_mask, const int* wave_out,
+                            double* det_acc, double det_scale, const float2* tw, cudaStream_t s);
+
+// Quadratic baseline: elastic probe waves in row-spectrum form.
+//   coef[b][j] = c exp(-2 pi i f (p_j Rx_b + q_j Ry_b)/L) computed in FP64 phase.
+cudaError_t launch_probe_init(float2* W, int n, int n_probes, const double* rx, const double* ry,
+                              const int* bp, const int* bq, int n_beams, int f, double cell,
+                              double c, const float2* tw, cudaStream_t s);
+
+// Quadratic baseline: new inelastic waves in row-pass output form from the
+// stored decimated transmitted elastic waves D (Eq. Hn0Psi on the N/2 grid).
+struct SpawnList {
+  const int* src;     // elastic wave index
+  const int* site;    // site index
+  const int* type;    // transition type
+  int count;
+  int first_wave;     // output wave index of the first spawn
+};
+cudaError_t launch_spawn(int n, const SpawnList& sp, const float2* D, const float2* H, int n_types,
+                         int w, const int* win_x0, const int* win_y0, float2* Phi, const float2* tw,
+                         cudaStream_t s);
+
+// Contraction (CUDA cores, FP32).
+struct TransitionBatch {
+  const int* site;    // [count] site index of each transition
+  const int* type;    // [count]
+  int count;
+};
+struct WindowLists {
+  const int* xoff; const int* xcnt; const int* xlist;   // per site: scan columns in the PRISM window
+  const int* yoff; const int* ycnt; const int* ylist;   // per site: scan rows
+  int max_nr;                                           // max over sites of xcnt*ycnt
+};
+cudaError_t launch_gemm1_fp32(const float2* Sout, const float2* Sin, int nh, int n_out, int n_in,
+                              int w, const float2* H, int n_types, const TransitionBatch& tb,
+                              const int* win_x0, const int* win_y0, float2* M, int64_t m_stride,
+                              cudaStream_t s);
+cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out, int n_in,
+                                   const float2* ax, const float2* ay, int n_sx, int n_sy,
+                                   const TransitionBatch& tb, const WindowLists& wl, double* map,
+                                   cudaStream_t s);
+// ax[j][ix] = exp(-2 pi i f p_j Rx(ix) / L) (FP64 phase); same for ay with q_j, Ry.
+cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
+                               double r0, double step, int n_pos, cudaStream_t s);
+cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
+
+}  // namespace eels

@@ -1,0 +1,379 @@
+// Band-limited plane-wave multislice on the GPU (Eqs. 3, 4, MSop, MSTop).
+//
+// A slice step psi -> F^-1[P F[t psi]] is split into two passes over a batch of
+// waves.  Between the passes every wave is kept in "row-spectrum" form: an
+// array [y][kx'] of N rows by N/2 columns holding the x-DFT of the wave restricted
+// to the band box |kx| < N/4 (column kx' < N/4 is frequency kx', otherwise
+// kx' - N/2).  Because the propagator limits every wave to p^2 + q^2 < (N/4)^2,
+// nothing outside the box is ever needed.
+//
+//   row pass    (one warp per row y):  zero-pad kx to N, inverse FFT_x, multiply
+//                by t (or conj t), optionally store the even samples (the N/2
+//                representation used by the S-matrices), forward FFT_x, keep the box.
+//   column pass (one warp per column kx'): FFT_y, keep the box, multiply by the
+//                propagator table (or its conjugate), zero-pad, inverse FFT_y.
+//
+// Scale convention: W holds the true row spectrum; the row pass produces N times
+// the true real-space wave and N times the true row spectrum, and the propagator
+// table carries the 1/N^2 that restores W after the column pass.
+#include "common.cuh"
+#include "internal.h"
+
+namespace eels {
+
+namespace {
+
+constexpr int kRowWarps = 8;   // rows per CTA in the row pass
+constexpr int kColCB = 8;      // columns per CTA in the column pass (one warp each)
+
+template <int N>
+__global__ void __launch_bounds__(kRowWarps * 32)
+k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
+           const float2* __restrict__ t_slice, int conj_t, int store_mode,
+           float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
+           const float2* __restrict__ tw_g) {
+  constexpr int NH = N / 2, NQ = N / 4;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* rows = smem + N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int y = blockIdx.x * kRowWarps + warp;
+  const int64_t wave = blockIdx.y;
+  float2* buf = rows + warp * N;
+  const float2* src = W + (wave * N + y) * NH;
+#pragma unroll 4
+  for (int k = lane; k < NH; k += 32) buf[k < NQ ? k : k + NH] = src[k];
+#pragma unroll 4
+  for (int k = NQ + lane; k < N - NQ; k += 32) buf[k] = make_float2(0.f, 0.f);
+  __syncwarp();
+  warp_fft<N, true>(buf, tw, lane);
+
+  const float2* trow = t_slice + (int64_t)y * N;
+  const bool store = store_mode != 0 && (y & 1) == 0 && wave < s_waves;
+  float2* srow = store ? S + wave * s_stride + (int64_t)(y >> 1) * NH : nullptr;
+#pragma unroll 4
+  for (int x = lane; x < N; x += 32) {
+    float2 v = buf[x];
+    if (store && store_mode == 2 && !(x & 1)) srow[x >> 1] = v;
+    const float2 t = trow[x];
+    v = conj_t ? cmulc(v, t) : cmul(v, t);
+    if (store && store_mode == 1 && !(x & 1)) srow[x >> 1] = v;
+    buf[x] = v;
+  }
+  if (!fft_out) return;
+  __syncwarp();
+  warp_fft<N, false>(buf, tw, lane);
+  float2* dst = Phi + (wave * N + y) * NH;
+#pragma unroll 4
+  for (int k = lane; k < NH; k += 32) dst[k] = buf[k < NQ ? k : k + NH];
+}
+
+template <int N>
+__global__ void __launch_bounds__(kColCB * 32)
+k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
+           const float2* __restrict__ ptab, int conj_p, int mode,
+           const uint8_t* __restrict__ det_mask, const int* __restrict__ wave_out,
+           double* __restrict__ det_acc, double det_scale, const float2* __restrict__ tw_g) {
+  constexpr int NH = N / 2, NQ = N / 4, LD = N + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* cols = smem + N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  const int kx0 = blockIdx.x * kColCB;
+  const int64_t wave = blockIdx.y;
+  const float2* src = Phi + wave * (int64_t)N * NH;
+  {
+    const int c = threadIdx.x % kColCB;
+#pragma unroll 4
+    for (int r = threadIdx.x / kColCB; r < N; r += (kColCB * 32) / kColCB)
+      cols[c * LD + r] = src[(int64_t)r * NH + kx0 + c];
+  }
+  __syncthreads();
+  float2* buf = cols + warp * LD;
+  const int kx = kx0 + warp;
+  warp_fft<N, false>(buf, tw, lane);
+  const float2* prow = ptab + (int64_t)kx * NH;
+  if (mode == 0) {
+#pragma unroll 4
+    for (int k = lane; k < N; k += 32) {
+      float2 v = make_float2(0.f, 0.f);
+      if (k < NQ || k >= N - NQ) {
+        const float2 p = prow[k < NQ ? k : k - NH];
+        v = conj_p ? cmulc(buf[k], p) : cmul(buf[k], p);
+      }
+      buf[k] = v;
+    }
+    __syncwarp();
+    warp_fft<N, true>(buf, tw, lane);
+    __syncthreads();
+    float2* dst = W + wave * (int64_t)N * NH;
+    const int c = threadIdx.x % kColCB;
+#pragma unroll 4
+    for (int r = threadIdx.x / kColCB; r < N; r += (kColCB * 32) / kColCB)
+      dst[(int64_t)r * NH + kx0 + c] = cols[c * LD + r];
+  } else {
+    const int out = wave_out[wave];
+    if (out < 0) return;
+    float acc = 0.f;
+    const uint8_t* mrow = det_mask + (int64_t)kx * NH;
+    for (int k = lane; k < N; k += 32) {
+      if (k < NQ || k >= N - NQ) {
+        const int ky = k < NQ ? k : k - NH;
+        if (mrow[ky]) {
+          const float2 v = conj_p ? cmulc(buf[k], prow[ky]) : cmul(buf[k], prow[ky]);
+          acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc != 0.f) atomicAdd(det_acc + out, det_scale * (double)acc);
+  }
+}
+
+__global__ void k_transmission(const float* __restrict__ v, double sigma, float2* __restrict__ t,
+                               int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(sigma * (double)v[i], &s, &c);
+    t[i] = make_float2((float)c, (float)s);
+  }
+}
+
+__global__ void k_propagator_table(float2* __restrict__ ptab, int n, double cell, double lam,
+                                   double dz, float scale) {
+  const int nh = n / 2, nq = n / 4;
+  const int total = nh * nh;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int a = i / nh, b = i % nh;             // [kx'][ky']
+    const int kx = a < nq ? a : a - nh;
+    const int ky = b < nq ? b : b - nh;
+    const int64_t k2 = (int64_t)kx * kx + (int64_t)ky * ky;
+    float2 p = make_float2(0.f, 0.f);
+    if (16 * k2 < (int64_t)n * n) {
+      // phase = -pi * lam * dz * |k|^2, argument (in units of pi) reduced mod 2 in FP64
+      double arg = lam * dz * (double)k2 / (cell * cell);
+      arg -= 2.0 * floor(0.5 * arg);
+      float s, c;
+      sincospif(-(float)arg, &s, &c);
+      p = make_float2(c * scale, s * scale);
+    }
+    ptab[i] = p;
+  }
+}
+
+__global__ void k_init_plane_waves(float2* __restrict__ W, int n, const int* __restrict__ px,
+                                   const int* __restrict__ py, const float2* __restrict__ amp,
+                                   const float2* __restrict__ tw) {
+  const int nh = n / 2;
+  const int64_t wave = blockIdx.y;
+  const int col = px[wave] >= 0 ? px[wave] : px[wave] + nh;
+  const int64_t per = (int64_t)n * nh;
+  float2* dst = W + wave * per;
+  const float2 a = amp[wave];
+  const int q = py[wave];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(i / nh), k = (int)(i % nh);
+    float2 v = make_float2(0.f, 0.f);
+    if (k == col) {
+      int m = (int)(((int64_t)q * y) % n);
+      if (m < 0) m += n;
+      v = cmul(a, cconj(tw[m]));   // exp(+2 pi i q y / N)
+    }
+    dst[i] = v;
+  }
+}
+
+__global__ void k_probe_init(float2* __restrict__ W, int n, const double* __restrict__ rx,
+                             const double* __restrict__ ry, const int* __restrict__ bp,
+                             const int* __restrict__ bq, int n_beams, int f, double cell,
+                             double c, const float2* __restrict__ tw) {
+  extern __shared__ float2 coef[];   // [n_beams]
+  const int nh = n / 2, nq = n / 4;
+  const int64_t wave = blockIdx.y;
+  for (int j = threadIdx.x; j < n_beams; j += blockDim.x) {
+    // a_j = c exp(-2 pi i f (p Rx + q Ry) / L), phase in cycles reduced in FP64
+    double cyc = (double)f * ((double)bp[j] * rx[wave] + (double)bq[j] * ry[wave]) / cell;
+    cyc -= floor(cyc);
+    double s, co;
+    sincospi(-2.0 * cyc, &s, &co);
+    coef[j] = make_float2((float)(c * co), (float)(c * s));
+  }
+  __syncthreads();
+  const int64_t per = (int64_t)n * nh;
+  float2* dst = W + wave * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(i / nh), k = (int)(i % nh);
+    const int kx = k < nq ? k : k - nh;
+    float2 v = make_float2(0.f, 0.f);
+    for (int j = 0; j < n_beams; ++j) {
+      if (f * bp[j] != kx) continue;
+      int m = (int)(((int64_t)f * bq[j] * y) % n);
+      if (m < 0) m += n;
+      v = cadd(v, cmul(coef[j], cconj(tw[m])));
+    }
+    dst[i] = v;
+  }
+}
+
+// One CTA per (output row y, spawn).  Writes the row-pass output form of the
+// inelastic wave Interp(H . D) of Eq. Hn0Psi: only even rows y = 2m carry the
+// N/2-grid row spectrum 4 * sum_u x(m,u) exp(-2 pi i kx u/(N/2)), odd rows are
+// zero; the column pass only looks at the band box of the y-spectrum, where this
+// equals the spectrum of the Fourier-interpolated wave.
+__global__ void k_spawn(int n, const int* __restrict__ src, const int* __restrict__ site,
+                        const int* __restrict__ type, int first_wave, const float2* __restrict__ D,
+                        const float2* __restrict__ H, int n_types, int w,
+                        const int* __restrict__ win_x0, const int* __restrict__ win_y0,
+                        float2* __restrict__ Phi, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  float2* xrow = sm;                 // [w] x(m, u) = H * D
+  int* gcol = (int*)(sm + w);        // [w] grid column of u
+  const int nh = n / 2, nq = n / 4;
+  const int y = blockIdx.x;
+  const int k = blockIdx.y;
+  const int s = site[k];
+  const int64_t wave = first_wave + k;
+  float2* dst = Phi + (wave * n + y) * nh;
+  int v = -1;
+  if ((y & 1) == 0) {
+    v = (y / 2 - win_y0[s]) % nh;
+    if (v < 0) v += nh;
+    if (v >= w) v = -1;
+  }
+  if (v < 0) {
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) dst[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float2* drow = D + (int64_t)src[k] * nh * nh + (int64_t)(y / 2) * nh;
+  const float2* hrow = H + (((int64_t)s * n_types + type[k]) * w + v) * w;
+  for (int u = threadIdx.x; u < w; u += blockDim.x) {
+    const int g = (win_x0[s] + u) % nh;
+    gcol[u] = g;
+    xrow[u] = cmul(hrow[u], drow[g]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    const int kx = i < nq ? i : i - nh;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int u = 0; u < w; ++u) {
+      int m = (int)(((int64_t)2 * kx * gcol[u]) % n);
+      if (m < 0) m += n;
+      acc = cadd(acc, cmul(xrow[u], tw[m]));   // exp(-2 pi i kx g / (N/2))
+    }
+    dst[i] = cscale(acc, 4.f);
+  }
+}
+
+template <int N>
+cudaError_t row_pass_n(int n_waves, const float2* W, float2* Phi, const float2* t, int conj_t,
+                       int store_mode, float2* S, int s_waves, int64_t s_stride, int fft_out,
+                       const float2* tw, cudaStream_t s) {
+  const size_t smem = (size_t)(N + kRowWarps * N) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_row_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N / kRowWarps, n_waves);
+  k_row_pass<N><<<grid, kRowWarps * 32, smem, s>>>(W, Phi, t, conj_t, store_mode, S, s_waves,
+                                                   s_stride, fft_out, tw);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t col_pass_n(int n_waves, const float2* Phi, float2* W, const float2* ptab, int conj_p,
+                       int mode, const uint8_t* det_mask, const int* wave_out, double* det_acc,
+                       double det_scale, const float2* tw, cudaStream_t s) {
+  const size_t smem = (size_t)(N + kColCB * (N + 1)) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_col_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N / 2 / kColCB, n_waves);
+  k_col_pass<N><<<grid, kColCB * 32, smem, s>>>(Phi, W, ptab, conj_p, mode, det_mask, wave_out,
+                                                det_acc, det_scale, tw);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define EELS_FOR_EACH_N(X) X(64) X(128) X(256) X(384) X(512) X(768) X(1024)
+
+bool grid_supported(int n) {
+#define EELS_CASE(NN) if (n == NN) return true;
+  EELS_FOR_EACH_N(EELS_CASE)
+#undef EELS_CASE
+  return false;
+}
+
+cudaError_t launch_row_pass(int n, int n_waves, const float2* W, float2* Phi, const float2* t,
+                            int conj_t, int store_mode, float2* S, int s_waves, int64_t s_stride,
+                            int fft_out, const float2* tw, cudaStream_t s) {
+  if (n_waves <= 0) return cudaSuccess;
+#define EELS_CASE(NN) \
+  if (n == NN) return row_pass_n<NN>(n_waves, W, Phi, t, conj_t, store_mode, S, s_waves, s_stride, fft_out, tw, s);
+  EELS_FOR_EACH_N(EELS_CASE)
+#undef EELS_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col_pass(int n, int n_waves, const float2* Phi, float2* W, const float2* ptab,
+                            int conj_p, int mode, const uint8_t* det_mask, const int* wave_out,
+                            double* det_acc, double det_scale, const float2* tw, cudaStream_t s) {
+  if (n_waves <= 0) return cudaSuccess;
+#define EELS_CASE(NN) \
+  if (n == NN) return col_pass_n<NN>(n_waves, Phi, W, ptab, conj_p, mode, det_mask, wave_out, det_acc, det_scale, tw, s);
+  EELS_FOR_EACH_N(EELS_CASE)
+#undef EELS_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_transmission(const float* v, double sigma, float2* t, int64_t count,
+                                cudaStream_t s) {
+  k_transmission<<<1184, 256, 0, s>>>(v, sigma, t, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagator_table(float2* ptab, int n, double cell, double lam, double dz,
+                                    float scale, cudaStream_t s) {
+  const int total = (n / 2) * (n / 2);
+  k_propagator_table<<<(total + 255) / 256, 256, 0, s>>>(ptab, n, cell, lam, dz, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_plane_waves(float2* W, int n, int n_waves, const int* px, const int* py,
+                                    const float2* amp, const float2* tw, cudaStream_t s) {
+  if (n_waves <= 0) return cudaSuccess;
+  const int64_t per = (int64_t)n * (n / 2);
+  dim3 grid((unsigned)((per + 255) / 256), n_waves);
+  k_init_plane_waves<<<grid, 256, 0, s>>>(W, n, px, py, amp, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_init(float2* W, int n, int n_probes, const double* rx, const double* ry,
+                              const int* bp, const int* bq, int n_beams, int f, double cell,
+                              double c, const float2* tw, cudaStream_t s) {
+  if (n_probes <= 0) return cudaSuccess;
+  const int64_t per = (int64_t)n * (n / 2);
+  dim3 grid((unsigned)((per + 255) / 256), n_probes);
+  k_probe_init<<<grid, 256, n_beams * sizeof(float2), s>>>(W, n, rx, ry, bp, bq, n_beams, f, cell,
+                                                           c, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spawn(int n, const SpawnList& sp, const float2* D, const float2* H, int n_types,
+                         int w, const int* win_x0, const int* win_y0, float2* Phi,
+                         const float2* tw, cudaStream_t s) {
+  if (sp.count <= 0) return cudaSuccess;
+  dim3 grid(n, sp.count);
+  const size_t smem = (size_t)w * (sizeof(float2) + sizeof(int));
+  k_spawn<<<grid, 256, smem, s>>>(n, sp.src, sp.site, sp.type, sp.first_wave, D, H, n_types, w,
+                                  win_x0, win_y0, Phi, tw);
+  return cudaGetLastError();
+}
+
+}  // namespace eels

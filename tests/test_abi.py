@@ -1,0 +1,77 @@
+"""The C-ABI library loads, exports every declared entry point, and its host-only
+helpers agree with the oracle and with the paper's printed memory example.
+No GPU needed (no compute call is made)."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import specimen as sp
+from oracle import multislice as ms
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stem_eels.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_07628_gb300 import build
+    build.build()
+    import paper_1908_07628_gb300 as g
+    return g
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(eels_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_three_calls_of_the_method():
+    syms = declared_symbols()
+    for name in ("eels_build_smatrix", "eels_inelastic_map", "eels_quadratic_reference_map"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(so, name), name
+    assert set(declared_symbols()) == set(lib.EXPORTS)
+
+
+def test_beam_counts_match_oracle_enumeration(lib):
+    """Integer work: the library's aperture enumeration equals the oracle's exactly."""
+    for (n, L, f, ang) in [(128, 8.6, 1, 0.02), (128, 8.6, 1, 0.03), (512, 34.4, 2, 0.02),
+                           (512, 34.4, 2, 0.03), (768, 51.6, 2, 0.03), (1024, 100.0, 4, 0.02),
+                           (1024, 100.0, 4, 0.03), (64, 6.0, 3, 0.05)]:
+        try:
+            ref = ms.lattice_beams(n, L, 0.02508, f, ang)[0].size
+        except ValueError:
+            continue
+        assert lib.count_beams(n, L, 0.02508, f, ang) == ref
+
+
+def test_memory_model_reproduces_paper_example(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_memory_example.json")))
+    conv, trans, smat = lib.memory_model(g["grid"], g["n_slices"], g["planes_s1"], g["planes_s2"])
+    assert int(conv / 1e6) == g["conventional_minimum_MB"]
+    assert round(trans / 1e9, 2) == g["transmission_GB"]
+    assert round(smat / 1e9, 2) == g["smatrix_GB"]
+
+
+def test_footprint_counts_stored_smatrix_and_one_sout_depth(lib):
+    n, nz, nin, nout, chunk = 512, 40, 593, 1321, 64
+    plane = 8 * (n // 2) ** 2
+    expect = 8 * nz * n * n + plane * (nz * nin + nout) + 2 * 8 * chunk * n * (n // 2)
+    assert lib.footprint_bytes(n, nz, nin, nout, chunk) == expect
+    assert lib.footprint_bytes(-2, nz, nin, nout, chunk) == -1
+
+
+def test_workload_beam_counts():
+    wl = sp.rocksalt_small()
+    assert ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)[0].size == 145
+    assert ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)[0].size == 333

@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance (FP32 multislice + FP32 contraction): normalised RMS map error
+eps = ||I_gpu - I_ref|| / ||I_ref|| <= 1e-4, the bound the design states for
+the FP32 path; S-matrix columns are compared with a relative tolerance of 1e-5
+per depth (FP32 FFT round-off grows like sqrt(log N) per step).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import specimen as sp
+from oracle import linear as lin
+from oracle import multislice as ms
+
+pytestmark = pytest.mark.gpu
+
+EPS_FP32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_07628_gb300 import build
+    build.build()
+    import paper_1908_07628_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    return g.Context(0)
+
+
+def eps(ref, test):
+    return ms.relative_error(ref, test)
+
+
+def _rand(n, f, seed, n_z=4, n_sites=6, w=8, cell=None, scan_n=3, n_types=2):
+    cell = cell if cell is not None else n * 0.05
+    return sp.random_workload(n=n, n_z=n_z, f=f, cell=cell, n_sites=n_sites, w=w, seed=seed,
+                              scan_n=scan_n, n_types=n_types, alpha=0.02, beta=0.03, dz=1.8)
+
+
+# --- S_in ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,f,seed", [(64, 1, 1), (128, 2, 2), (384, 2, 3)])
+def test_s_in_matches_oracle(g, ctx, n, f, seed):
+    import torch
+    wl = _rand(n, f, seed, n_z=3)
+    sm = g.build_smatrix_for(ctx, wl)
+    ref, (bp, bq) = lin.build_s_in(wl)
+    p, q = sm.beams()
+    assert np.array_equal(p, bp) and np.array_equal(q, bq)
+    for depth in range(wl.n_z):
+        out = torch.empty((sm.n_in, n // 2, n // 2), dtype=torch.complex64, device="cuda")
+        sm.copy_depth(depth, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.complex128) / n
+        err = np.linalg.norm(got - ref[depth]) / np.linalg.norm(ref[depth])
+        assert err < 1e-5, (depth, err)
+
+
+# --- maps -----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,f,seed,w", [(64, 1, 4, 8), (64, 2, 5, 13), (128, 3, 6, 20),
+                                        (256, 2, 7, 32), (384, 3, 8, 24)])
+def test_linear_map_fp32_matches_oracle(g, ctx, n, f, seed, w):
+    wl = _rand(n, f, seed, w=w, n_sites=8)
+    ref = lin.linear_map(wl) if n >= 256 else ms.quadratic_map(wl)
+    sm = g.build_smatrix_for(ctx, wl)
+    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    assert ref.max() > 0
+    assert eps(ref, got) < EPS_FP32
+
+
+def test_rocksalt_small_full_map(g, ctx):
+    wl = sp.rocksalt_small()
+    ref = lin.linear_map(wl)
+    q = ms.quadratic_map(wl, positions=[(0, 0), (5, 2)])
+    for iy, ix in [(0, 0), (5, 2)]:
+        assert np.allclose(q[:, iy, ix], ref[:, iy, ix], rtol=1e-12, atol=0)
+    sm = g.build_smatrix_for(ctx, wl)
+    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    assert eps(ref, got) < EPS_FP32
+    for m in range(wl.n_types):
+        assert eps(ref[m], got[m]) < EPS_FP32
+
+
+def test_quadratic_reference_map_matches_oracle(g, ctx):
+    wl = _rand(64, 2, 9, n_sites=5)
+    ref = ms.quadratic_map(wl)
+    c = {}
+    ms.quadratic_map(wl, positions=[(0, 0)], counter=c)
+    got, steps = g.quadratic_reference_map_for(ctx, wl)
+    assert eps(ref, got) < EPS_FP32
+    # the GPU count is the paper's per-probe count summed over probes
+    c_all = {}
+    ms.quadratic_map(wl, counter=c_all)
+    assert steps == c_all["steps"]
+
+
+def test_quadratic_reference_subset_positions(g, ctx):
+    wl = sp.rocksalt_small()
+    pos = [(1, 3), (6, 7)]
+    ref = ms.quadratic_map(wl, positions=pos)
+    got, steps = g.quadratic_reference_map_for(ctx, wl, positions=pos)
+    assert eps(ref, got) < EPS_FP32
+    assert steps == 2 * (24 * 21 + 6)
+
+
+# --- edge cases -------------------------------------------------------------------------
+
+def test_no_sites_gives_zero_map(g, ctx):
+    wl = _rand(64, 1, 10).with_sites([])
+    sm = g.build_smatrix_for(ctx, wl)
+    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    assert got.shape == (wl.n_types, wl.scan[1], wl.scan[0]) and not got.any()
+
+
+def test_single_slice_and_extreme_windows(g, ctx):
+    for w in (1, 32):
+        wl = _rand(64, 1, 11 + w, n_z=1, w=w, n_sites=3)
+        ref = ms.quadratic_map(wl)
+        sm = g.build_smatrix_for(ctx, wl)
+        got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+        assert eps(ref, got) < EPS_FP32
+
+
+def test_site_outside_every_window_contributes_nothing(g, ctx):
+    wl = _rand(128, 4, 12, n_sites=4)
+    rx, ry = wl.scan_positions()
+    far_x = (rx[0] + wl.cell / 2) % wl.cell      # half a cell away: outside the L/4 window
+    wl.site_x[:] = far_x
+    sm = g.build_smatrix_for(ctx, wl)
+    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    assert not got.any()
+
+
+def test_window_rule_tie_is_half_open(g, ctx):
+    """A site exactly at -L/(2f) from a probe counts, one at +L/(2f) does not."""
+    wl = _rand(64, 2, 13, n_sites=2, n_z=2)
+    rx, ry = wl.scan_positions()
+    h = wl.cell / (2 * wl.f)
+    wl.site_x[:] = [rx[1] - h, rx[1] + h]
+    wl.site_y[:] = ry[1]
+    ref = ms.quadratic_map(wl)
+    sm = g.build_smatrix_for(ctx, wl)
+    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    assert eps(ref, got) < EPS_FP32
+
+
+def test_errors_are_reported(g, ctx):
+    wl = _rand(64, 1, 14)
+    with pytest.raises(g.EelsError) as e:
+        ctx.build_smatrix(np.zeros((2, 96, 96), np.float32), 10.0, 0.02508, 7e-4, 2.0, 1, 0.02)
+    assert e.value.status == 2
+    with pytest.raises(g.EelsError) as e:
+        ctx.build_smatrix(wl.vproj, wl.cell, wl.lam, wl.sigma, wl.dz, 1, 0.5)  # beyond band
+    assert e.value.status == 1
+    sm = g.build_smatrix_for(ctx, wl)
+    with pytest.raises(g.EelsError) as e:
+        ctx.inelastic_map(sm, np.zeros((1, 1, 40, 40), np.complex64), [0], [0], [0], [0.0], [0.0],
+                          wl.scan, wl.beta)
+    assert e.value.status == 1
+
+
+# --- full-size workload, sampled outputs -----------------------------------------------------
+
+def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
+    """The bench workload's S-matrix (512^2, 40 slices, f = 2) with three sites at three
+    depths; the oracle evaluates the conventional algorithm at sampled probes."""
+    wl = sp.rocksalt_fp32()
+    rx, ry = wl.scan_positions()
+    cx, cy = rx[16], ry[16]
+    cand = [s for s in range(wl.n_sites)
+            if abs(wl.site_x[s] - cx) < 3.0 and abs(wl.site_y[s] - cy) < 3.0]
+    chosen = []
+    for target in (0, 21, 39):
+        for s in cand:
+            if wl.site_slice[s] == target:
+                chosen.append(s)
+                break
+    assert len(chosen) == 3
+    sub = wl.with_sites(chosen)
+    sm = g.build_smatrix_for(ctx, sub)
+    got = g.inelastic_map_for(ctx, sm, sub, "fp32")
+    pos = [(16, 16), (3, 29), (30, 5)]
+    ref = ms.quadratic_map(sub, positions=pos)
+    r = np.array([ref[:, iy, ix] for iy, ix in pos])
+    t = np.array([got[:, iy, ix] for iy, ix in pos])
+    assert r.max() > 0
+    assert eps(r, t) < EPS_FP32
