@@ -35,6 +35,7 @@ DEFAULT_WORKLOAD = "rocksalt_fp32"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
 SMS, FP32_LANES = 152, 128
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def _peaks():
@@ -286,6 +287,14 @@ def gpu_arm(args, rank, world):
             roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                     "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+        elif "tf32" in dom:
+            flops = contraction_flops(wl, n_in, n_out, dom)
+            # TF32 dense = 1.1 / 2.25 of BF16 (nominal); the kernel runs inside a long step
+            peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+            achieved = flops / launches / avg_s / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": "measured bf16 sustained x nominal tf32/bf16 (1.1/2.25)"}
         else:
             flops = contraction_flops(wl, n_in, n_out, dom)
             mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -300,7 +309,7 @@ def gpu_arm(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32" if args.precision == "tf32" else "f32", "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "n_in": n_in,
                    "n_out": n_out, "scan": [wl.scan[0], wl.scan[1]], "n_types": wl.n_types,
                    "precision": args.precision, "parallelism": f"replicas{world}",
@@ -317,18 +326,29 @@ def gpu_arm(args, rank, world):
     return line
 
 
+def _window_count(s, r, cell, f):
+    """Scan positions whose PRISM window (minimum image within [-L/2f, L/2f)) holds s."""
+    d = s - r
+    d = d - cell * np.floor(d / cell + 0.5)
+    h = cell / (2 * f)
+    return int(((d >= -h) & (d < h)).sum())
+
+
 def contraction_flops(wl, n_in, n_out, kernel):
     """Real flops of the contraction kernels over the whole workload (8 per complex MAC)."""
-    from oracle import multislice as ms   # window rule only, to count work
     rx, ry = wl.scan_positions()
     g1 = g2 = 0
     for s in range(wl.n_sites):
-        nx = int(ms.axis_in_window(wl.site_x[s], rx, wl.cell, wl.f).sum())
-        ny = int(ms.axis_in_window(wl.site_y[s], ry, wl.cell, wl.f).sum())
+        nx = _window_count(wl.site_x[s], rx, wl.cell, wl.f)
+        ny = _window_count(wl.site_y[s], ry, wl.cell, wl.f)
         if nx and ny:
             g1 += wl.n_types * n_out * wl.w * wl.w * n_in
             g2 += wl.n_types * n_out * n_in * nx * ny
-    return 8.0 * (g1 if "gemm1" in kernel else g2)
+    if "gemm1" in kernel:
+        return 8.0 * g1
+    if "gemm2" in kernel:
+        return 8.0 * g2
+    return 8.0 * (g1 + g2)
 
 
 def reference_arm(args, rank, world):
@@ -362,7 +382,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sp.WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--quad-probes", type=int, default=8)
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -156,10 +156,11 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 
 /* Per-kernel device timing.  While enabled, every kernel launch made by calls on
  * this context is bracketed by CUDA events recorded on the launch stream.
- * eels_profile_read synchronises those events and writes a JSON object
- * {"kernel": {"launches": L, "ms": T}, ...} (NUL-terminated, at most cap bytes)
- * and returns the number of bytes the full text needs; the records are then
- * cleared.  Disabled by default. */
+ * eels_profile_read synchronises those events, folds them into running totals
+ * and returns the number of bytes the JSON text {"kernel": {"launches": L,
+ * "ms": T}, ...} needs (with its NUL).  If buf holds at least that many bytes
+ * the text is written there and the totals are reset; otherwise nothing is
+ * lost and the call can be repeated with a larger buffer.  Disabled by default. */
 eels_status eels_profile_enable(eels_ctx* ctx, int on);
 int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
 

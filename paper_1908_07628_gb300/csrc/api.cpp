@@ -26,6 +26,7 @@ struct eels_ctx {
   struct Rec { const char* name; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> spare;
+  std::map<std::string, std::pair<int64_t, double>> prof_totals;
 };
 
 struct eels_smatrix {
@@ -225,12 +226,12 @@ eels_status eels_profile_enable(eels_ctx* ctx, int on) {
 int eels_profile_read(eels_ctx* ctx, char* buf, int cap) {
   if (!ctx) return -1;
   cudaSetDevice(ctx->device);
-  std::map<std::string, std::pair<int64_t, double>> agg;
+  // fold pending event pairs into the running totals
   for (auto& r : ctx->recs) {
     float ms = 0.f;
     cudaEventSynchronize(r.b);
     cudaEventElapsedTime(&ms, r.a, r.b);
-    auto& e = agg[r.name];
+    auto& e = ctx->prof_totals[r.name];
     e.first += 1;
     e.second += ms;
     ctx->spare.push_back(r.a);
@@ -238,7 +239,7 @@ int eels_profile_read(eels_ctx* ctx, char* buf, int cap) {
   }
   ctx->recs.clear();
   std::string out = "{";
-  for (auto& kv : agg) {
+  for (auto& kv : ctx->prof_totals) {
     char tmp[256];
     std::snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}",
                   out.size() > 1 ? ", " : "", kv.first.c_str(), (long long)kv.second.first,
@@ -246,11 +247,14 @@ int eels_profile_read(eels_ctx* ctx, char* buf, int cap) {
     out += tmp;
   }
   out += "}";
-  if (buf && cap > 0) {
-    std::strncpy(buf, out.c_str(), (size_t)cap - 1);
-    buf[cap - 1] = 0;
+  const int need = (int)out.size() + 1;
+  if (buf && cap >= need) {
+    std::memcpy(buf, out.c_str(), (size_t)need);
+    ctx->prof_totals.clear();   // totals are handed over once, then start again
+  } else if (buf && cap > 0) {
+    buf[0] = 0;
   }
-  return (int)out.size() + 1;
+  return need;
 }
 
 int eels_count_beams(int n, double cell, double lambda, int f, double angle) {
@@ -429,8 +433,9 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
   eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
   if (r != EELS_OK) return r;
-  if (precision != EELS_PREC_FP32)
+  if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32)
     return fail(ctx, EELS_ERR_UNSUPPORTED, "precision not built");
+  const bool tc = precision == EELS_PREC_TF32;
   if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
   EELS_CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -522,7 +527,55 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   for (int i = 0; i < n_z; ++i) max_tr = std::max(max_tr, (int)tr_site[i].size());
   const int batch = (int)std::max<int64_t>(1, std::min<int64_t>(
       std::max(max_tr, 1), (int64_t)(1 << 30) / (m_stride * (int64_t)sizeof(float2))));
-  EELS_CK(M.alloc((size_t)batch * m_stride, st));
+  if (!tc) EELS_CK(M.alloc((size_t)batch * m_stride, st));
+
+  // tensor-core path: sites of a slice in batches of `sb` slots
+  auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  const int k1p = (int)rup(2 * (int64_t)w * w, 32), k2p = (int)rup(2 * (int64_t)n_in, 32);
+  const int nr_cap = std::max(L.max_nr, 1);
+  const int64_t per_site = 4 * ((int64_t)n_out * k1p + (int64_t)T * 2 * n_in * k1p +
+                                (int64_t)T * n_out * k2p + (int64_t)2 * nr_cap * k2p);
+  int max_sites = 0;
+  std::vector<std::vector<int>> slice_sites(n_z);
+  for (int s = 0; s < S; ++s)
+    if (L.xcnt[s] > 0 && L.ycnt[s] > 0) slice_sites[tr->slice[s]].push_back(s);
+  for (int i = 0; i < n_z; ++i) max_sites = std::max(max_sites, (int)slice_sites[i].size());
+  const int sb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(max_sites, 1),
+                                                             ((int64_t)3 << 30) / per_site));
+  DevBuf<float> A1, B1, M1, B2;
+  DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus;
+  std::vector<int> slot_all, zs_all, zt_all, nv2_all, site_off(n_z + 1, 0);
+  if (tc) {
+    for (int i = 0; i < n_z; ++i) {
+      site_off[i] = (int)slot_all.size();
+      for (int s : slice_sites[i]) {
+        slot_all.push_back(s);
+        for (int m = 0; m < T; ++m) {
+          zs_all.push_back(s);
+          zt_all.push_back(m);
+          nv2_all.push_back(2 * L.xcnt[s] * L.ycnt[s]);
+        }
+      }
+    }
+    site_off[n_z] = (int)slot_all.size();
+    std::vector<int> ab1(sb * T), bb1(sb * T), nv1(sb * T, k2p), ab2(sb * T), bb2(sb * T);
+    for (int z = 0; z < sb * T; ++z) { ab1[z] = z / T; bb1[z] = z; ab2[z] = z; bb2[z] = z / T; }
+    EELS_CK(dslot.upload(slot_all.data(), slot_all.size(), st));
+    EELS_CK(dzs.upload(zs_all.data(), zs_all.size(), st));
+    EELS_CK(dzt.upload(zt_all.data(), zt_all.size(), st));
+    EELS_CK(dnv2.upload(nv2_all.data(), nv2_all.size(), st));
+    EELS_CK(dab1.upload(ab1.data(), ab1.size(), st));
+    EELS_CK(dbb1.upload(bb1.data(), bb1.size(), st));
+    EELS_CK(dnv1.upload(nv1.data(), nv1.size(), st));
+    EELS_CK(dab2.upload(ab2.data(), ab2.size(), st));
+    EELS_CK(dbb2.upload(bb2.data(), bb2.size(), st));
+    EELS_CK(dstatus.alloc(1, st));
+    EELS_CK(cudaMemsetAsync(dstatus.p, 0, sizeof(int), st));
+    EELS_CK(A1.alloc((size_t)sb * n_out * k1p, st));
+    EELS_CK(B1.alloc((size_t)sb * T * 2 * n_in * k1p, st));
+    EELS_CK(M1.alloc((size_t)sb * T * n_out * k2p, st));
+    EELS_CK(B2.alloc((size_t)sb * 2 * nr_cap * k2p, st));
+  }
 
   {
     Prof pr(ctx, "init_plane_waves", st);
@@ -537,7 +590,34 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
                               plane, i > 0 ? 1 : 0, tw, st));
     }
     const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
-    for (int b0 = slice_off[i]; b0 < slice_off[i + 1]; b0 += batch) {
+    for (int q0 = site_off[i]; tc && q0 < site_off[i + 1]; q0 += sb) {
+      const int ns = std::min(sb, site_off[i + 1] - q0);
+      eels::TcBatch b{};
+      b.Sout = Sout.p; b.Sin = Sin; b.nh = nh; b.n_out = n_out; b.n_in = n_in; b.w = w;
+      b.n_types = T; b.H = H; b.wx = dwx.p; b.wy = dwy.p;
+      b.slot_site = dslot.p + q0; b.z_site = dzs.p + (int64_t)q0 * T;
+      b.z_type = dzt.p + (int64_t)q0 * T; b.n_sites = ns; b.slots_cap = sb;
+      b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
+      b.ax = ax.p; b.ay = ay.p; b.n_sx = sc->n_sx; b.n_sy = sc->n_sy;
+      b.xoff = dxoff.p; b.xcnt = dxcnt.p; b.xlist = dxlist.p;
+      b.yoff = dyoff.p; b.ycnt = dycnt.p; b.ylist = dylist.p; b.nr_cap = nr_cap;
+      b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;
+      b.a_batch2 = dab2.p; b.b_batch2 = dbb2.p; b.n_valid2 = dnv2.p + (int64_t)q0 * T;
+      b.map = dmap.p; b.status = dstatus.p;
+      {
+        Prof pr(ctx, "tc_gather", st);
+        EELS_CK(eels::tc_gather(b, st));
+      }
+      {
+        Prof pr(ctx, "gemm1_tf32", st);
+        EELS_CK(eels::tc_gemm1(b, st));
+      }
+      {
+        Prof pr(ctx, "gemm2_abs2_tf32", st);
+        EELS_CK(eels::tc_gemm2(b, st));
+      }
+    }
+    for (int b0 = slice_off[i]; !tc && b0 < slice_off[i + 1]; b0 += batch) {
       eels::TransitionBatch tb{dts.p + b0, dtt.p + b0, std::min(batch, slice_off[i + 1] - b0)};
       {
         Prof pr(ctx, "gemm1_fp32", st);
@@ -562,6 +642,12 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
   EELS_CK(eels::launch_scale(dmap.p, n_map, scale, st));
+  if (tc) {
+    int flag = 0;
+    EELS_CK(cudaMemcpyAsync(&flag, dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EELS_CK(cudaStreamSynchronize(st));
+    if (flag) return fail(ctx, EELS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+  }
   if (map_on_device) {
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
   } else {

@@ -81,4 +81,30 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
                                double r0, double step, int n_pos, cudaStream_t s);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
 
+// Tensor-core (tcgen05, TF32) contraction of a batch of sites of one slice:
+// gathers the windowed operands, runs GEMM 1 (M = Sout^H diag(H) Sin) and GEMM 2
+// with the fused sum_d |.|^2 epilogue into map.  All pointers are device memory.
+struct TcBatch {
+  const float2* Sout; const float2* Sin;  // depth planes [beam][nh][nh]
+  int nh, n_out, n_in, w, n_types;
+  const float2* H;                        // [S][T][w][w]
+  const int* wx; const int* wy;           // per site window origin
+  const int* slot_site;                   // [n_sites] site of each slot of this batch
+  const int* z_site; const int* z_type;   // [n_sites * T] transition z = slot*T + type
+  int n_sites, slots_cap;                 // sites in this batch, buffer capacity in sites
+  int k1p, k2p;                           // padded K of GEMM 1 (2 w^2) and GEMM 2 (2 n_in)
+  float* A1; float* B1; float* M1; float* B2;
+  const float2* ax; const float2* ay; int n_sx, n_sy;
+  const int* xoff; const int* xcnt; const int* xlist;
+  const int* yoff; const int* ycnt; const int* ylist;
+  int nr_cap;                             // max scan positions of a site
+  const int* a_batch1; const int* b_batch1; const int* n_valid1;
+  const int* a_batch2; const int* b_batch2; const int* n_valid2;
+  double* map;
+  int* status;                            // set to 1 if a bounded wait timed out
+};
+cudaError_t tc_gather(const TcBatch& b, cudaStream_t s);   // A1, B1, B2 operand buffers
+cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t s);    // M1 = GEMM 1
+cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t s);    // map += sum_d |GEMM 2|^2
+
 }  // namespace eels

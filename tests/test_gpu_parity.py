@@ -17,6 +17,9 @@ from oracle import multislice as ms
 pytestmark = pytest.mark.gpu
 
 EPS_FP32 = 1e-4
+# tensor-core path: operands rounded to TF32 (unit roundoff 2^-11), FP32 accumulate
+EPS_TC = 1e-3
+EPS = {"fp32": EPS_FP32, "tf32": EPS_TC}
 
 
 @pytest.fixture(scope="module")
@@ -68,13 +71,14 @@ def test_s_in_matches_oracle(g, ctx, n, f, seed):
 
 @pytest.mark.parametrize("n,f,seed,w", [(64, 1, 4, 8), (64, 2, 5, 13), (128, 3, 6, 20),
                                         (256, 2, 7, 32), (384, 3, 8, 24)])
-def test_linear_map_fp32_matches_oracle(g, ctx, n, f, seed, w):
+def test_linear_map_matches_oracle(g, ctx, n, f, seed, w):
     wl = _rand(n, f, seed, w=w, n_sites=8)
     ref = lin.linear_map(wl) if n >= 256 else ms.quadratic_map(wl)
     sm = g.build_smatrix_for(ctx, wl)
-    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
     assert ref.max() > 0
-    assert eps(ref, got) < EPS_FP32
+    for prec in ("fp32", "tf32"):
+        got = g.inelastic_map_for(ctx, sm, wl, prec)
+        assert eps(ref, got) < EPS[prec], prec
 
 
 def test_rocksalt_small_full_map(g, ctx):
@@ -84,10 +88,11 @@ def test_rocksalt_small_full_map(g, ctx):
     for iy, ix in [(0, 0), (5, 2)]:
         assert np.allclose(q[:, iy, ix], ref[:, iy, ix], rtol=1e-12, atol=0)
     sm = g.build_smatrix_for(ctx, wl)
-    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
-    assert eps(ref, got) < EPS_FP32
-    for m in range(wl.n_types):
-        assert eps(ref[m], got[m]) < EPS_FP32
+    for prec in ("fp32", "tf32"):
+        got = g.inelastic_map_for(ctx, sm, wl, prec)
+        assert eps(ref, got) < EPS[prec], prec
+        for m in range(wl.n_types):
+            assert eps(ref[m], got[m]) < EPS[prec], (prec, m)
 
 
 def test_quadratic_reference_map_matches_oracle(g, ctx):
@@ -117,8 +122,9 @@ def test_quadratic_reference_subset_positions(g, ctx):
 def test_no_sites_gives_zero_map(g, ctx):
     wl = _rand(64, 1, 10).with_sites([])
     sm = g.build_smatrix_for(ctx, wl)
-    got = g.inelastic_map_for(ctx, sm, wl, "fp32")
-    assert got.shape == (wl.n_types, wl.scan[1], wl.scan[0]) and not got.any()
+    for prec in ("fp32", "tf32"):
+        got = g.inelastic_map_for(ctx, sm, wl, prec)
+        assert got.shape == (wl.n_types, wl.scan[1], wl.scan[0]) and not got.any()
 
 
 def test_single_slice_and_extreme_windows(g, ctx):
@@ -126,8 +132,9 @@ def test_single_slice_and_extreme_windows(g, ctx):
         wl = _rand(64, 1, 11 + w, n_z=1, w=w, n_sites=3)
         ref = ms.quadratic_map(wl)
         sm = g.build_smatrix_for(ctx, wl)
-        got = g.inelastic_map_for(ctx, sm, wl, "fp32")
-        assert eps(ref, got) < EPS_FP32
+        for prec in ("fp32", "tf32"):
+            got = g.inelastic_map_for(ctx, sm, wl, prec)
+            assert eps(ref, got) < EPS[prec], (w, prec)
 
 
 def test_site_outside_every_window_contributes_nothing(g, ctx):
@@ -187,10 +194,11 @@ def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
     assert len(chosen) == 3
     sub = wl.with_sites(chosen)
     sm = g.build_smatrix_for(ctx, sub)
-    got = g.inelastic_map_for(ctx, sm, sub, "fp32")
     pos = [(16, 16), (3, 29), (30, 5)]
     ref = ms.quadratic_map(sub, positions=pos)
     r = np.array([ref[:, iy, ix] for iy, ix in pos])
-    t = np.array([got[:, iy, ix] for iy, ix in pos])
     assert r.max() > 0
-    assert eps(r, t) < EPS_FP32
+    for prec in ("fp32", "tf32"):
+        got = g.inelastic_map_for(ctx, sm, sub, prec)
+        t = np.array([got[:, iy, ix] for iy, ix in pos])
+        assert eps(r, t) < EPS[prec], prec
