@@ -182,6 +182,33 @@ def _algorithmic(wl, n_in, n_out, prof):
     return out
 
 
+def _source_hash(kernel):
+    import hashlib
+    files = (["paper_1908_07628_gb300/csrc/multislice.cu", "paper_1908_07628_gb300/csrc/common.cuh"]
+             if "pass" in kernel else
+             ["paper_1908_07628_gb300/csrc/contract_tc.cu", "paper_1908_07628_gb300/csrc/tc_ptx.cuh"])
+    m = hashlib.sha1()
+    for f in files:
+        m.update(open(os.path.join(ROOT, f), "rb").read())
+    return m.hexdigest()[:12]
+
+
+def measured_traffic(kernel, n, waves):
+    """DRAM bytes per launch from the committed ncu table, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        if ln.startswith("#") or not ln.strip():
+            continue
+        name, nn, w, sha, nbytes = ln.split()
+        if name == kernel and int(nn) == n and w == str(waves) and sha == _source_hash(kernel):
+            return float(nbytes)
+    return None
+
+
 def gpu_arm(args, rank, world):
     import torch
     from paper_1908_07628_gb300 import build
@@ -190,7 +217,7 @@ def gpu_arm(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    wl = sp.WORKLOADS[args.workload]()
+    wl = load_workload(args)
     ctx = g.Context(dev)
     stream = torch.cuda.current_stream()
     vdev = torch.from_numpy(wl.vproj).cuda()
@@ -284,8 +311,11 @@ def gpu_arm(args, rank, world):
         avg_s = prof[dom]["ms"] / launches / 1e3
         if dom in alg and alg[dom][0] == "hbm":
             achieved = alg[dom][1] / avg_s / 1e9
+            waves = n_out if "adjoint" in dom else n_in
             roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": measured_traffic(dom, wl.n, waves),
+                    "algorithmic_bytes": alg[dom][1],
                     "peak_source": "measured" if "fallback" not in peaks else "fallback"}
         elif "tf32" in dom:
             flops = contraction_flops(wl, n_in, n_out, dom)
@@ -351,6 +381,18 @@ def contraction_flops(wl, n_in, n_out, kernel):
     return 8.0 * (g1 + g2)
 
 
+def load_workload(args):
+    wl = sp.WORKLOADS[args.workload]()
+    if args.max_slices and args.max_slices < wl.n_z:
+        k = args.max_slices
+        keep = np.nonzero(wl.site_slice < k)[0]
+        wl = wl.with_sites(keep)
+        wl.vproj = np.ascontiguousarray(wl.vproj[:k])
+        wl.n_z = k
+        wl.name = f"{wl.name}_first{k}slices"
+    return wl
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return None
@@ -386,6 +428,8 @@ def main():
     ap.add_argument("--quad-probes", type=int, default=8)
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-slices", type=int, default=0,
+                    help="keep only the first K slices (smaller device footprint for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

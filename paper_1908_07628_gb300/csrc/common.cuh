@@ -122,6 +122,105 @@ __device__ __forceinline__ void dft<3, false>(float2* u) { dft3<false>(u); }
 template <>
 __device__ __forceinline__ void dft<3, true>(float2* u) { dft3<true>(u); }
 
+// ---------------------------------------------------------------------------
+// Register-resident warp FFT.
+//
+// A length-N sequence is spread over the 32 lanes of a warp.  For a stage of
+// radix R the lane holds x[b + q N/R] for its butterflies b = lane + 32 t
+// (t < ceil(N/R/32)) in v[t R + q].  Between stages the outputs are exchanged
+// through the warp's padded shared-memory buffer (Stockham order); the first
+// stage reads and the last stage leaves its data in registers.  The last stage of
+// a Stockham pass writes x[b + q N/R], the same layout the first stage of a pass
+// with the same radix reads, so an inverse transform run with the reversed radix
+// plan feeds a forward transform (and vice versa) without any exchange.
+// ---------------------------------------------------------------------------
+template <int N, bool REV>
+struct Plan {
+  static constexpr int NS = plan_len(N);
+  __host__ __device__ static constexpr int R(int s) {
+    return REV ? plan_radix(N, NS - 1 - s) : plan_radix(N, s);
+  }
+  __host__ __device__ static constexpr int P(int s) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= R(i);
+    return p;
+  }
+  __host__ __device__ static constexpr int elems(int s) {
+    return ((N / R(s) + 31) / 32) * R(s);
+  }
+  __host__ __device__ static constexpr int max_elems() {
+    int m = 0;
+    for (int i = 0; i < NS; ++i) m = elems(i) > m ? elems(i) : m;
+    return m;
+  }
+};
+
+template <int N>
+struct RegFFT {
+  static constexpr int E = Plan<N, false>::max_elems() > Plan<N, true>::max_elems()
+                               ? Plan<N, false>::max_elems()
+                               : Plan<N, true>::max_elems();
+};
+
+// padded shared-memory index: one spare slot every 8 elements
+__device__ __forceinline__ int spad(int j) { return j + (j >> 3); }
+__host__ __device__ constexpr int spad_len(int n) { return n + n / 8; }
+
+template <int N, bool INV, bool REV, int S>
+__device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf,
+                                              const float2* __restrict__ tw, int lane) {
+  using PL = Plan<N, REV>;
+  constexpr int R = PL::R(S), P = PL::P(S), NB = N / R, PER = (NB + 31) / 32;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int b = lane + 32 * t;
+    if (NB % 32 == 0 || b < NB) {
+      if constexpr (P > 1) {
+        const int k = b % P;
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          float2 w = __ldg(tw + q * k * (N / (P * R)));
+          if (INV) w.y = -w.y;
+          v[t * R + q] = cmul(v[t * R + q], w);
+        }
+      }
+      dft<R, INV>(v + t * R);
+    }
+  }
+  if constexpr (S + 1 < PL::NS) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int b = lane + 32 * t;
+      if (NB % 32 == 0 || b < NB) {
+        const int k = b % P;
+        const int j0 = (b - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) sbuf[spad(j0 + q * P)] = v[t * R + q];
+      }
+    }
+    __syncwarp();
+    constexpr int R2 = PL::R(S + 1), NB2 = N / R2, PER2 = (NB2 + 31) / 32;
+#pragma unroll
+    for (int t = 0; t < PER2; ++t) {
+      const int b = lane + 32 * t;
+      if (NB2 % 32 == 0 || b < NB2) {
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[t * R2 + q] = sbuf[spad(b + q * NB2)];
+      }
+    }
+    __syncwarp();
+    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, tw, lane);
+  }
+}
+
+// Transform the warp-held sequence.  On entry v holds x[b + q N/R0] (R0 = first
+// radix of the plan), on exit X[b + q N/RL] (RL = last radix).  tw[n] = exp(-2 pi i n/N).
+template <int N, bool INV, bool REV>
+__device__ __forceinline__ void reg_fft(float2* v, float2* sbuf, const float2* __restrict__ tw,
+                                        int lane) {
+  reg_fft_stage<N, INV, REV, 0>(v, sbuf, tw, lane);
+}
+
 // One warp transforms buf[0..N) in place (Stockham autosort, natural order in
 // and out).  tw[n] = exp(-2 pi i n / N) for n in [0, N).  Stage s with radix R
 // and P = product of the earlier radices: butterfly b reads buf[b + q N/R],

@@ -31,43 +31,80 @@ __global__ void __launch_bounds__(kRowWarps * 32)
 k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
            const float2* __restrict__ t_slice, int conj_t, int store_mode,
            float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
-           const float2* __restrict__ tw_g) {
+           const float2* __restrict__ tw) {
   constexpr int NH = N / 2, NQ = N / 4;
+  using PI = Plan<N, true>;    // inverse transform: reversed radix plan
+  using PF = Plan<N, false>;   // forward transform
+  constexpr int E = RegFFT<N>::E;
   extern __shared__ float2 smem[];
-  float2* tw = smem;
-  float2* rows = smem + N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
-  __syncthreads();
+  float2* sbuf = smem + warp * spad_len(N);
   const int y = blockIdx.x * kRowWarps + warp;
   const int64_t wave = blockIdx.y;
-  float2* buf = rows + warp * N;
   const float2* src = W + (wave * N + y) * NH;
-#pragma unroll 4
-  for (int k = lane; k < NH; k += 32) buf[k < NQ ? k : k + NH] = src[k];
-#pragma unroll 4
-  for (int k = NQ + lane; k < N - NQ; k += 32) buf[k] = make_float2(0.f, 0.f);
-  __syncwarp();
-  warp_fft<N, true>(buf, tw, lane);
+  float2 v[E];
 
-  const float2* trow = t_slice + (int64_t)y * N;
-  const bool store = store_mode != 0 && (y & 1) == 0 && wave < s_waves;
-  float2* srow = store ? S + wave * s_stride + (int64_t)(y >> 1) * NH : nullptr;
-#pragma unroll 4
-  for (int x = lane; x < N; x += 32) {
-    float2 v = buf[x];
-    if (store && store_mode == 2 && !(x & 1)) srow[x >> 1] = v;
-    const float2 t = trow[x];
-    v = conj_t ? cmulc(v, t) : cmul(v, t);
-    if (store && store_mode == 1 && !(x & 1)) srow[x >> 1] = v;
-    buf[x] = v;
+  // inputs of the inverse x-FFT: the band box, zero-padded to N
+  {
+    constexpr int R0 = PI::R(0), NB0 = N / R0, PER0 = (NB0 + 31) / 32;
+#pragma unroll
+    for (int t = 0; t < PER0; ++t) {
+      const int b = lane + 32 * t;
+#pragma unroll
+      for (int q = 0; q < R0; ++q) {
+        const int pos = b + q * NB0;
+        float2 x = make_float2(0.f, 0.f);
+        if ((NB0 % 32 == 0 || b < NB0) && (q * NB0 < NQ || q * NB0 >= N - NQ))
+          x = src[pos < NQ ? pos : pos - NH];
+        v[t * R0 + q] = x;
+      }
+    }
+  }
+  reg_fft<N, true, true>(v, sbuf, tw, lane);
+
+  // real space: v[t RL + q] = N psi(x = b + q N/RL, y)
+  {
+    constexpr int RL = PF::R(0), NBL = N / RL, PERL = (NBL + 31) / 32;
+    const float2* trow = t_slice + (int64_t)y * N;
+    const bool store = store_mode != 0 && (y & 1) == 0 && wave < s_waves;
+    float2* srow = store ? S + wave * s_stride + (int64_t)(y >> 1) * NH : nullptr;
+#pragma unroll
+    for (int t = 0; t < PERL; ++t) {
+      const int b = lane + 32 * t;
+      if (NBL % 32 == 0 || b < NBL) {
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          const int x = b + q * NBL;
+          float2 val = v[t * RL + q];
+          if (store && store_mode == 2 && !(x & 1)) srow[x >> 1] = val;
+          const float2 tt = trow[x];
+          val = conj_t ? cmulc(val, tt) : cmul(val, tt);
+          if (store && store_mode == 1 && !(x & 1)) srow[x >> 1] = val;
+          v[t * RL + q] = val;
+        }
+      }
+    }
   }
   if (!fft_out) return;
   __syncwarp();
-  warp_fft<N, false>(buf, tw, lane);
-  float2* dst = Phi + (wave * N + y) * NH;
-#pragma unroll 4
-  for (int k = lane; k < NH; k += 32) dst[k] = buf[k < NQ ? k : k + NH];
+  reg_fft<N, false, false>(v, sbuf, tw, lane);
+  {
+    constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = (NBF + 31) / 32;
+    float2* dst = Phi + (wave * N + y) * NH;
+#pragma unroll
+    for (int t = 0; t < PERF; ++t) {
+      const int b = lane + 32 * t;
+      if (NBF % 32 == 0 || b < NBF) {
+#pragma unroll
+        for (int q = 0; q < RF; ++q) {
+          if (q * NBF < NQ || q * NBF >= N - NQ) {
+            const int pos = b + q * NBF;
+            dst[pos < NQ ? pos : pos - NH] = v[t * RF + q];
+          }
+        }
+      }
+    }
+  }
 }
 
 template <int N>
@@ -75,56 +112,94 @@ __global__ void __launch_bounds__(kColCB * 32)
 k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
            const float2* __restrict__ ptab, int conj_p, int mode,
            const uint8_t* __restrict__ det_mask, const int* __restrict__ wave_out,
-           double* __restrict__ det_acc, double det_scale, const float2* __restrict__ tw_g) {
-  constexpr int NH = N / 2, NQ = N / 4, LD = N + 1;
+           double* __restrict__ det_acc, double det_scale, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, NQ = N / 4;
+  constexpr int LD = spad_len(N) + 2;   // column stride: keeps the tile load conflict-free
+  using PI = Plan<N, true>;
+  using PF = Plan<N, false>;
+  constexpr int E = RegFFT<N>::E;
   extern __shared__ float2 smem[];
-  float2* tw = smem;
-  float2* cols = smem + N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
   const int kx0 = blockIdx.x * kColCB;
   const int64_t wave = blockIdx.y;
   const float2* src = Phi + wave * (int64_t)N * NH;
   {
     const int c = threadIdx.x % kColCB;
 #pragma unroll 4
-    for (int r = threadIdx.x / kColCB; r < N; r += (kColCB * 32) / kColCB)
-      cols[c * LD + r] = src[(int64_t)r * NH + kx0 + c];
+    for (int r = threadIdx.x / kColCB; r < N; r += 32)
+      smem[c * LD + spad(r)] = src[(int64_t)r * NH + kx0 + c];
   }
   __syncthreads();
-  float2* buf = cols + warp * LD;
+  float2* sbuf = smem + warp * LD;
   const int kx = kx0 + warp;
-  warp_fft<N, false>(buf, tw, lane);
+  float2 v[E];
+  {
+    constexpr int R0 = PF::R(0), NB0 = N / R0, PER0 = (NB0 + 31) / 32;
+#pragma unroll
+    for (int t = 0; t < PER0; ++t) {
+      const int b = lane + 32 * t;
+      if (NB0 % 32 == 0 || b < NB0) {
+#pragma unroll
+        for (int q = 0; q < R0; ++q) v[t * R0 + q] = sbuf[spad(b + q * NB0)];
+      }
+    }
+  }
+  __syncwarp();
+  reg_fft<N, false, false>(v, sbuf, tw, lane);
+  // y-spectrum in registers at ky = b + q N/RF: keep the box, multiply by the propagator
+  constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = (NBF + 31) / 32;
   const float2* prow = ptab + (int64_t)kx * NH;
   if (mode == 0) {
-#pragma unroll 4
-    for (int k = lane; k < N; k += 32) {
-      float2 v = make_float2(0.f, 0.f);
-      if (k < NQ || k >= N - NQ) {
-        const float2 p = prow[k < NQ ? k : k - NH];
-        v = conj_p ? cmulc(buf[k], p) : cmul(buf[k], p);
+#pragma unroll
+    for (int t = 0; t < PERF; ++t) {
+      const int b = lane + 32 * t;
+#pragma unroll
+      for (int q = 0; q < RF; ++q) {
+        float2 val = make_float2(0.f, 0.f);
+        if ((NBF % 32 == 0 || b < NBF) && (q * NBF < NQ || q * NBF >= N - NQ)) {
+          const int pos = b + q * NBF;
+          const float2 p = prow[pos < NQ ? pos : pos - NH];
+          val = conj_p ? cmulc(v[t * RF + q], p) : cmul(v[t * RF + q], p);
+        }
+        v[t * RF + q] = val;
       }
-      buf[k] = v;
     }
     __syncwarp();
-    warp_fft<N, true>(buf, tw, lane);
+    reg_fft<N, true, true>(v, sbuf, tw, lane);
+    {
+      constexpr int RL = PI::R(PI::NS - 1), NBL = N / RL, PERL = (NBL + 31) / 32;
+#pragma unroll
+      for (int t = 0; t < PERL; ++t) {
+        const int b = lane + 32 * t;
+        if (NBL % 32 == 0 || b < NBL) {
+#pragma unroll
+          for (int q = 0; q < RL; ++q) sbuf[spad(b + q * NBL)] = v[t * RL + q];
+        }
+      }
+    }
     __syncthreads();
     float2* dst = W + wave * (int64_t)N * NH;
     const int c = threadIdx.x % kColCB;
 #pragma unroll 4
-    for (int r = threadIdx.x / kColCB; r < N; r += (kColCB * 32) / kColCB)
-      dst[(int64_t)r * NH + kx0 + c] = cols[c * LD + r];
+    for (int r = threadIdx.x / kColCB; r < N; r += 32)
+      dst[(int64_t)r * NH + kx0 + c] = smem[c * LD + spad(r)];
   } else {
     const int out = wave_out[wave];
     if (out < 0) return;
     float acc = 0.f;
     const uint8_t* mrow = det_mask + (int64_t)kx * NH;
-    for (int k = lane; k < N; k += 32) {
-      if (k < NQ || k >= N - NQ) {
-        const int ky = k < NQ ? k : k - NH;
-        if (mrow[ky]) {
-          const float2 v = conj_p ? cmulc(buf[k], prow[ky]) : cmul(buf[k], prow[ky]);
-          acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+#pragma unroll
+    for (int t = 0; t < PERF; ++t) {
+      const int b = lane + 32 * t;
+#pragma unroll
+      for (int q = 0; q < RF; ++q) {
+        if ((NBF % 32 == 0 || b < NBF) && (q * NBF < NQ || q * NBF >= N - NQ)) {
+          const int pos = b + q * NBF;
+          const int ky = pos < NQ ? pos : pos - NH;
+          if (mrow[ky]) {
+            const float2 val = conj_p ? cmulc(v[t * RF + q], prow[ky]) : cmul(v[t * RF + q], prow[ky]);
+            acc = fmaf(val.x, val.x, fmaf(val.y, val.y, acc));
+          }
         }
       }
     }
@@ -275,7 +350,7 @@ template <int N>
 cudaError_t row_pass_n(int n_waves, const float2* W, float2* Phi, const float2* t, int conj_t,
                        int store_mode, float2* S, int s_waves, int64_t s_stride, int fft_out,
                        const float2* tw, cudaStream_t s) {
-  const size_t smem = (size_t)(N + kRowWarps * N) * sizeof(float2);
+  const size_t smem = (size_t)kRowWarps * spad_len(N) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_row_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -289,7 +364,7 @@ template <int N>
 cudaError_t col_pass_n(int n_waves, const float2* Phi, float2* W, const float2* ptab, int conj_p,
                        int mode, const uint8_t* det_mask, const int* wave_out, double* det_acc,
                        double det_scale, const float2* tw, cudaStream_t s) {
-  const size_t smem = (size_t)(N + kColCB * (N + 1)) * sizeof(float2);
+  const size_t smem = (size_t)kColCB * (spad_len(N) + 2) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_col_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
