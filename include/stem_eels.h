@@ -164,6 +164,34 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 eels_status eels_profile_enable(eels_ctx* ctx, int on);
 int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
 
+/* Size of the static device work array used by eels_build_smatrix_static. */
+#define EELS_STATIC_SCRATCH_BYTES (64ull << 20)
+
+/* S_in build that allocates nothing (the paper has no counterpart: this is a
+ * deployment variant of eels_build_smatrix).  For callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph is being captured, plug-ins whose
+ * host application owns or has reserved the device memory, real-time loops that
+ * must not risk an allocation failure -- it writes what eels_build_smatrix stores,
+ * S_in(i) for every depth as complex64 [n_z][n_in][N/2][N/2] scaled by N, into the
+ * caller's device buffer s_in (s_in_bytes long), and keeps all its work arrays in
+ * one static device array of EELS_STATIC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.  vproj may be host or device memory; it takes no
+ * context and reports errors as a status plus text in err (err_cap bytes).
+ * *n_in_out receives the number of probe beams.
+ * - The first call on a device looks up the device address of the static array
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ * - Every call on a device shares the array and leaves its contents behind;
+ *   calls whose GPU work overlaps (different streams or threads) race.
+ * - Waves are processed in chunks sized to the static array (at N = 512 about 30
+ *   waves per chunk, at N = 1024 six).
+ * - EELS_ERR_ARG if s_in_bytes < n_z n_in (N/2)^2 * 8 or if not even one N x N/2
+ *   complex64 work wave pair plus one slice of tables fits in the static array;
+ *   EELS_ERR_UNSUPPORTED for an unbuilt grid size. */
+eels_status eels_build_smatrix_static(const eels_specimen* spec, const eels_optics* optics,
+                                      float* s_in, int64_t s_in_bytes, int* n_in_out,
+                                      void* stream, char* err, int err_cap);
+
 /* Number of f-lattice beams with lambda |k| <= angle (Sec. III, pi alpha^2 L^2 / f^2). */
 int eels_count_beams(int n, double cell, double lambda, int f, double angle);
 

@@ -4,6 +4,7 @@ Brown, Ciston & Ophus, arXiv 1908.07628.  The computation lives in the CUDA
 library libstemeels.so (C ABI in include/stem_eels.h); this package only builds
 it and marshals arguments to it.
 """
-from ._lib import (Context, EelsError, SMatrix, build_smatrix_for, count_beams,  # noqa: F401
+from ._lib import (Context, EelsError, SMatrix, build_smatrix_for, build_smatrix_static,  # noqa: F401
+                   count_beams,
                    footprint_bytes, inelastic_map_for, load, memory_model,
                    quadratic_reference_map_for, EXPORTS, LIB_PATH)

@@ -68,6 +68,9 @@ EXPORTS = {
                                                C.c_void_p, C.POINTER(C.c_int64)]),
     "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
+    "eels_build_smatrix_static": (C.c_int, [C.POINTER(Specimen), C.POINTER(Optics), C.c_void_p,
+                                            C.c_int64, C.POINTER(C.c_int), C.c_void_p,
+                                            C.c_char_p, C.c_int]),
     "eels_count_beams": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double]),
     "eels_memory_model": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     "eels_footprint_bytes": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -272,6 +275,27 @@ def _transitions(H, site_slice, win_x0, win_y0, site_x, site_y):
     ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
     tr = Transitions(int(H.shape[0]), int(H.shape[1]), int(H.shape[2]), h, *ptrs, h_dev)
     return tr, (hk, arrs)
+
+
+def build_smatrix_static(vproj, cell, lam, sigma, dz, f, alpha, out, stream=None) -> int:
+    """eels_build_smatrix_static: S_in into the complex64 CUDA tensor `out`
+    ([n_z][n_in][N/2][N/2]) using only the library's static work array.  Returns n_in."""
+    v, on_dev, keep = _ptr(vproj, np.float32)
+    n_z, n = int(vproj.shape[0]), int(vproj.shape[-1])
+    spec = Specimen(n, n_z, float(cell), v, on_dev)
+    op = Optics(float(lam), float(sigma), float(dz), int(f), float(alpha))
+    optr, o_dev, okeep = _ptr(out, np.complex64)
+    if not o_dev:
+        raise TypeError("out must be a CUDA tensor")
+    n_in = C.c_int(0)
+    err = C.create_string_buffer(256)
+    st = load().eels_build_smatrix_static(C.byref(spec), C.byref(op), optr,
+                                          int(out.numel() * out.element_size()), C.byref(n_in),
+                                          _stream(stream), err, len(err))
+    del keep, okeep
+    if st != 0:
+        raise EelsError(st, "eels_build_smatrix_static: " + err.value.decode())
+    return int(n_in.value)
 
 
 def count_beams(n, cell, lam, f, angle) -> int:
