@@ -309,6 +309,7 @@ def gpu_arm(args, rank, world):
     if dom is not None:
         launches = prof[dom]["launches"]
         avg_s = prof[dom]["ms"] / launches / 1e3
+        per_step = launches / args.steps          # launches of this kernel in one step
         if dom in alg and alg[dom][0] == "hbm":
             achieved = alg[dom][1] / avg_s / 1e9
             waves = n_out if "adjoint" in dom else n_in
@@ -321,7 +322,7 @@ def gpu_arm(args, rank, world):
             flops = contraction_flops(wl, n_in, n_out, dom)
             # TF32 dense = 1.1 / 2.25 of BF16 (nominal); the kernel runs inside a long step
             peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
-            achieved = flops / launches / avg_s / 1e12
+            achieved = flops / per_step / avg_s / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": "measured bf16 sustained x nominal tf32/bf16 (1.1/2.25)"}
@@ -329,7 +330,7 @@ def gpu_arm(args, rank, world):
             flops = contraction_flops(wl, n_in, n_out, dom)
             mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
             peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
-            achieved = flops / launches / avg_s / 1e12
+            achieved = flops / per_step / avg_s / 1e12
             roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}

@@ -1,5 +1,5 @@
-// Device helpers shared by the STEM-EELS kernels: complex float2 arithmetic and a
-// warp-synchronous mixed-radix Stockham FFT operating on one row in shared memory.
+// Device helpers shared by the STEM-EELS kernels: complex float2 arithmetic, small
+// in-register DFTs and a register-resident mixed-radix Stockham FFT run by one warp.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,10 +25,31 @@ __device__ __forceinline__ float2 mul_i(float2 a) {
 }
 
 // ---------------------------------------------------------------------------
-// Radix plan: N = 3^a 2^b.  Radix-3 stages first, then radix-8 stages, and the
-// remaining factor of the power of two as 4, 4x4 or 2.
-// ---------------------------------------------------------------------------
+// Radix plans.  Two-stage plans with in-register radix-16/32 butterflies for the common
+// power-of-two grids (one shared-memory exchange per transform).
+__host__ __device__ constexpr int plan2_radix(int n, int s) {
+  return n == 256 ? (s < 2 ? 16 : 0)
+       : n == 512 ? (s == 0 ? 16 : s == 1 ? 32 : 0)
+       : n == 1024 ? (s < 2 ? 32 : 0)
+       : -1;
+}
+
+__host__ __device__ constexpr int plan_len_generic(int n);
+__host__ __device__ constexpr int plan_radix_generic(int n, int s);
+
 __host__ __device__ constexpr int plan_len(int n) {
+  return plan2_radix(n, 0) > 0 ? 2 : plan_len_generic(n);
+}
+__host__ __device__ constexpr int plan_radix(int n, int s) {
+  return plan2_radix(n, 0) > 0 ? plan2_radix(n, s) : plan_radix_generic(n, s);
+}
+
+// Sequences per warp: two where a single sequence would leave lanes idle in a stage.
+__host__ __device__ constexpr int rows_per_warp(int n) { return (n == 256 || n == 512) ? 2 : 1; }
+
+// Generic plan for N = 3^a 2^b: radix-3 stages first, then radix-8 stages, and the
+// remaining factor of the power of two as 4, 4x4 or 2.
+__host__ __device__ constexpr int plan_len_generic(int n) {
   int c = 0;
   while (n % 3 == 0) { ++c; n /= 3; }
   int b = 0;
@@ -38,7 +59,7 @@ __host__ __device__ constexpr int plan_len(int n) {
   return c + (b - 2) / 3 + 1;
 }
 
-__host__ __device__ constexpr int plan_radix(int n, int s) {
+__host__ __device__ constexpr int plan_radix_generic(int n, int s) {
   int c = 0;
   int m = n;
   while (m % 3 == 0) { ++c; m /= 3; }
@@ -122,6 +143,60 @@ __device__ __forceinline__ void dft<3, false>(float2* u) { dft3<false>(u); }
 template <>
 __device__ __forceinline__ void dft<3, true>(float2* u) { dft3<true>(u); }
 
+// exp(2 pi i m / 32) components, FP64-rounded to FP32
+__host__ __device__ constexpr float cos32(int m) {
+  constexpr float c[32] = {1.0f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f,
+                           7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f,
+                           0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
+                           -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
+                           -1.0f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
+                           -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f,
+                           0.0f, 1.950903220e-01f, 3.826834324e-01f, 5.555702330e-01f,
+                           7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f};
+  return c[m & 31];
+}
+__host__ __device__ constexpr float sin32(int m) { return cos32(m - 8); }
+
+// In-register DFT of length R = R1 R2: n = R2 n1 + n2, k = k1 + R1 k2;
+// DFT_R1 over n1, twiddle exp(+-2 pi i n2 k1 / R), DFT_R2 over n2.
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void dft_composite(float2* x) {
+  constexpr int R = R1 * R2;
+  constexpr int SC = 32 / R;
+  constexpr float SG = INV ? 1.f : -1.f;
+  float2 y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    float2 t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[R2 * n1 + n2];
+    dft<R1, INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const int m = (n2 * k1) % R;
+      y[n2 * R1 + k1] = m == 0 ? t[k1]
+                               : cmul(t[k1], make_float2(cos32(m * SC), SG * sin32(m * SC)));
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+    dft<R2, INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
+  }
+}
+template <>
+__device__ __forceinline__ void dft<16, false>(float2* u) { dft_composite<4, 4, false>(u); }
+template <>
+__device__ __forceinline__ void dft<16, true>(float2* u) { dft_composite<4, 4, true>(u); }
+template <>
+__device__ __forceinline__ void dft<32, false>(float2* u) { dft_composite<8, 4, false>(u); }
+template <>
+__device__ __forceinline__ void dft<32, true>(float2* u) { dft_composite<8, 4, true>(u); }
+
 // ---------------------------------------------------------------------------
 // Register-resident warp FFT.
 //
@@ -137,6 +212,7 @@ __device__ __forceinline__ void dft<3, true>(float2* u) { dft3<true>(u); }
 template <int N, bool REV>
 struct Plan {
   static constexpr int NS = plan_len(N);
+  static constexpr int ROWS = rows_per_warp(N);
   __host__ __device__ static constexpr int R(int s) {
     return REV ? plan_radix(N, NS - 1 - s) : plan_radix(N, s);
   }
@@ -145,9 +221,9 @@ struct Plan {
     for (int i = 0; i < s; ++i) p *= R(i);
     return p;
   }
-  __host__ __device__ static constexpr int elems(int s) {
-    return ((N / R(s) + 31) / 32) * R(s);
-  }
+  // butterflies of all ROWS sequences of a stage, spread over the 32 lanes
+  __host__ __device__ static constexpr int per(int s) { return (ROWS * (N / R(s)) + 31) / 32; }
+  __host__ __device__ static constexpr int elems(int s) { return per(s) * R(s); }
   __host__ __device__ static constexpr int max_elems() {
     int m = 0;
     for (int i = 0; i < NS; ++i) m = elems(i) > m ? elems(i) : m;
@@ -157,32 +233,81 @@ struct Plan {
 
 template <int N>
 struct RegFFT {
+  static constexpr int ROWS = rows_per_warp(N);
   static constexpr int E = Plan<N, false>::max_elems() > Plan<N, true>::max_elems()
                                ? Plan<N, false>::max_elems()
                                : Plan<N, true>::max_elems();
 };
 
-// padded shared-memory index: one spare slot every 8 elements
-__device__ __forceinline__ int spad(int j) { return j + (j >> 3); }
-__host__ __device__ constexpr int spad_len(int n) { return n + n / 8; }
+// Padded shared-memory index: one spare slot every PAD elements.  A first stage of
+// radix R writes x[R b + q] and the next stage of a two-stage plan reads
+// x[b + R q]; with PAD = R both map a half-warp onto distinct banks.
+template <int PAD>
+__device__ __forceinline__ int spad(int j) { return j + j / PAD; }
+__host__ __device__ constexpr int spad_len(int n) { return n + n / 8; }   // largest padding used
 
+// Exchange padding of a transform: its first radix for two-stage plans, 8 otherwise.
+template <int N, bool REV>
+__host__ __device__ constexpr int pad_of() {
+  return plan2_radix(N, 0) > 0 ? (REV ? plan_radix(N, plan_len(N) - 1) : plan_radix(N, 0)) : 8;
+}
+
+// Twiddles exp(-+2 pi i q k s / N) for q = 1..R-1 of one butterfly: one or two table
+// loads and products (at most six roundings) instead of R - 1 loads.
+template <int N, int R, bool INV>
+__device__ __forceinline__ void twiddles(float2* w, int ks, const float2* __restrict__ tw) {
+  if constexpr (R <= 4) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      w[q] = __ldg(tw + q * ks);
+      if (INV) w[q].y = -w[q].y;
+    }
+  } else {
+    w[1] = __ldg(tw + ks);
+    if (INV) w[1].y = -w[1].y;
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+    w[4] = cmul(w[2], w[2]);
+    if constexpr (R > 4) {
+#pragma unroll
+      for (int q = 5; q < (R < 8 ? R : 8); ++q) w[q] = cmul(w[4], w[q - 4]);
+    }
+    if constexpr (R > 8) {
+      float2 w8 = __ldg(tw + ((8 * ks) % N));
+      if (INV) w8.y = -w8.y;
+      float2 hi = w8;
+#pragma unroll
+      for (int a = 1; a < R / 8; ++a) {
+        w[8 * a] = hi;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) w[8 * a + q] = cmul(hi, w[q]);
+        hi = cmul(hi, w8);
+      }
+    }
+  }
+}
+
+// Butterfly slot u = lane + 32 t of a stage with NB butterflies per sequence
+// belongs to sequence u / NB, butterfly u % NB.  Sequence r lives at
+// sbuf + r * ld in the warp's shared buffer.
 template <int N, bool INV, bool REV, int S>
-__device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf,
+__device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
                                               const float2* __restrict__ tw, int lane) {
   using PL = Plan<N, REV>;
-  constexpr int R = PL::R(S), P = PL::P(S), NB = N / R, PER = (NB + 31) / 32;
+  constexpr int ROWS = PL::ROWS;
+  constexpr int PAD = pad_of<N, REV>();
+  constexpr int R = PL::R(S), P = PL::P(S), NB = N / R, PER = PL::per(S);
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
-    const int b = lane + 32 * t;
-    if (NB % 32 == 0 || b < NB) {
+    const int u = lane + 32 * t;
+    if ((ROWS * NB) % 32 == 0 || u < ROWS * NB) {
+      const int b = u % NB;
       if constexpr (P > 1) {
         const int k = b % P;
+        float2 w[R];
+        twiddles<N, R, INV>(w, k * (N / (P * R)), tw);
 #pragma unroll
-        for (int q = 1; q < R; ++q) {
-          float2 w = __ldg(tw + q * k * (N / (P * R)));
-          if (INV) w.y = -w.y;
-          v[t * R + q] = cmul(v[t * R + q], w);
-        }
+        for (int q = 1; q < R; ++q) v[t * R + q] = cmul(v[t * R + q], w[q]);
       }
       dft<R, INV>(v + t * R);
     }
@@ -190,80 +315,40 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf,
   if constexpr (S + 1 < PL::NS) {
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-      const int b = lane + 32 * t;
-      if (NB % 32 == 0 || b < NB) {
+      const int u = lane + 32 * t;
+      if ((ROWS * NB) % 32 == 0 || u < ROWS * NB) {
+        const int b = u % NB;
         const int k = b % P;
         const int j0 = (b - k) * R + k;
+        float2* row = sbuf + (u / NB) * ld;
 #pragma unroll
-        for (int q = 0; q < R; ++q) sbuf[spad(j0 + q * P)] = v[t * R + q];
+        for (int q = 0; q < R; ++q) row[spad<PAD>(j0 + q * P)] = v[t * R + q];
       }
     }
     __syncwarp();
-    constexpr int R2 = PL::R(S + 1), NB2 = N / R2, PER2 = (NB2 + 31) / 32;
+    constexpr int R2 = PL::R(S + 1), NB2 = N / R2, PER2 = PL::per(S + 1);
 #pragma unroll
     for (int t = 0; t < PER2; ++t) {
-      const int b = lane + 32 * t;
-      if (NB2 % 32 == 0 || b < NB2) {
+      const int u = lane + 32 * t;
+      if ((ROWS * NB2) % 32 == 0 || u < ROWS * NB2) {
+        const int b = u % NB2;
+        const float2* row = sbuf + (u / NB2) * ld;
 #pragma unroll
-        for (int q = 0; q < R2; ++q) v[t * R2 + q] = sbuf[spad(b + q * NB2)];
+        for (int q = 0; q < R2; ++q) v[t * R2 + q] = row[spad<PAD>(b + q * NB2)];
       }
     }
     __syncwarp();
-    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, tw, lane);
+    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, ld, tw, lane);
   }
 }
 
-// Transform the warp-held sequence.  On entry v holds x[b + q N/R0] (R0 = first
-// radix of the plan), on exit X[b + q N/RL] (RL = last radix).  tw[n] = exp(-2 pi i n/N).
+// Transform the ROWS warp-held sequences.  On entry slot u of v holds
+// x_{u/NB0}[u%NB0 + q N/R0] (R0 = first radix), on exit X in the same form for the
+// last radix.  tw[n] = exp(-2 pi i n/N).
 template <int N, bool INV, bool REV>
-__device__ __forceinline__ void reg_fft(float2* v, float2* sbuf, const float2* __restrict__ tw,
-                                        int lane) {
-  reg_fft_stage<N, INV, REV, 0>(v, sbuf, tw, lane);
-}
-
-// One warp transforms buf[0..N) in place (Stockham autosort, natural order in
-// and out).  tw[n] = exp(-2 pi i n / N) for n in [0, N).  Stage s with radix R
-// and P = product of the earlier radices: butterfly b reads buf[b + q N/R],
-// multiplies by exp(-+2 pi i q (b mod P) / (P R)), does a radix-R DFT and writes
-// buf[(b - b mod P) R + b mod P + q P].
-template <int N, bool INV, int STAGE = 0, int P = 1>
-__device__ __forceinline__ void warp_fft(float2* buf, const float2* __restrict__ tw, int lane) {
-  constexpr int R = plan_radix(N, STAGE);
-  if constexpr (R != 0) {
-    constexpr int NB = N / R;
-    constexpr int PER = (NB + 31) / 32;
-    float2 u[PER][R];
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int b = lane + 32 * t;
-      if (NB % 32 == 0 || b < NB) {
-#pragma unroll
-        for (int q = 0; q < R; ++q) u[t][q] = buf[b + q * NB];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int b = lane + 32 * t;
-      if (NB % 32 == 0 || b < NB) {
-        const int k = b % P;
-        if constexpr (P > 1) {
-#pragma unroll
-          for (int q = 1; q < R; ++q) {
-            float2 w = tw[q * k * (N / (P * R))];
-            if (INV) w.y = -w.y;
-            u[t][q] = cmul(u[t][q], w);
-          }
-        }
-        dft<R, INV>(u[t]);
-        const int j = (b - k) * R + k;
-#pragma unroll
-        for (int q = 0; q < R; ++q) buf[j + q * P] = u[t][q];
-      }
-    }
-    __syncwarp();
-    warp_fft<N, INV, STAGE + 1, P * R>(buf, tw, lane);
-  }
+__device__ __forceinline__ void reg_fft(float2* v, float2* sbuf, int ld,
+                                        const float2* __restrict__ tw, int lane) {
+  reg_fft_stage<N, INV, REV, 0>(v, sbuf, ld, tw, lane);
 }
 
 }  // namespace eels

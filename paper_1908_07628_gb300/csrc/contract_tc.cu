@@ -144,13 +144,26 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         p[q] = live ? fmaf(v[2 * q], v[2 * q], v[2 * q + 1] * v[2 * q + 1]) : 0.f;
+      // reduce-scatter over the 32 rows of the warp: halve the value set at each of the
+      // lane bits 4, 3, 2, then sum over bits 1, 0.  Lane L ends with the warp total of
+      // value ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
+      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+      float r4[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 4; ++q) {
+        const float send = b4 ? p[q] : p[q + 4];
+        r4[q] = (b4 ? p[q + 4] : p[q]) + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+      float r2[2];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_xor_sync(0xffffffffu, p[q], o);
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) atomicAdd(&red[c / 2 + q], p[q]);
+      for (int q = 0; q < 2; ++q) {
+        const float send = b3 ? r4[q] : r4[q + 2];
+        r2[q] = (b3 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      float r1 = (b2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r2[0] : r2[1], 4);
+      r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+      r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+      if ((lane & 3) == 0) atomicAdd(&red[c / 2 + (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)], r1);
     }
     __syncthreads();
     const int s = ea.z_site[z];

@@ -33,45 +33,49 @@ k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
            float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
            const float2* __restrict__ tw) {
   constexpr int NH = N / 2, NQ = N / 4;
+  constexpr int ROWS = RegFFT<N>::ROWS;
+  constexpr int LDR = spad_len(N);
   using PI = Plan<N, true>;    // inverse transform: reversed radix plan
   using PF = Plan<N, false>;   // forward transform
   constexpr int E = RegFFT<N>::E;
   extern __shared__ float2 smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* sbuf = smem + warp * spad_len(N);
-  const int y = blockIdx.x * kRowWarps + warp;
+  float2* sbuf = smem + warp * ROWS * LDR;
+  const int y0 = (blockIdx.x * kRowWarps + warp) * ROWS;   // rows y0 .. y0 + ROWS - 1
   const int64_t wave = blockIdx.y;
-  const float2* src = W + (wave * N + y) * NH;
   float2 v[E];
 
   // inputs of the inverse x-FFT: the band box, zero-padded to N
   {
-    constexpr int R0 = PI::R(0), NB0 = N / R0, PER0 = (NB0 + 31) / 32;
+    constexpr int R0 = PI::R(0), NB0 = N / R0, PER0 = PI::per(0);
 #pragma unroll
     for (int t = 0; t < PER0; ++t) {
-      const int b = lane + 32 * t;
+      const int u = lane + 32 * t;
+      const bool live = (ROWS * NB0) % 32 == 0 || u < ROWS * NB0;
+      const int b = u % NB0;
+      const float2* src = W + (wave * N + y0 + u / NB0) * NH;
 #pragma unroll
       for (int q = 0; q < R0; ++q) {
         const int pos = b + q * NB0;
         float2 x = make_float2(0.f, 0.f);
-        if ((NB0 % 32 == 0 || b < NB0) && (q * NB0 < NQ || q * NB0 >= N - NQ))
-          x = src[pos < NQ ? pos : pos - NH];
+        if (live && (q * NB0 < NQ || q * NB0 >= N - NQ)) x = src[pos < NQ ? pos : pos - NH];
         v[t * R0 + q] = x;
       }
     }
   }
-  reg_fft<N, true, true>(v, sbuf, tw, lane);
+  reg_fft<N, true, true>(v, sbuf, LDR, tw, lane);
 
-  // real space: v[t RL + q] = N psi(x = b + q N/RL, y)
+  // real space: slot u holds N psi(x = u%NBL + q N/RL, y0 + u/NBL)
   {
-    constexpr int RL = PF::R(0), NBL = N / RL, PERL = (NBL + 31) / 32;
-    const float2* trow = t_slice + (int64_t)y * N;
-    const bool store = store_mode != 0 && (y & 1) == 0 && wave < s_waves;
-    float2* srow = store ? S + wave * s_stride + (int64_t)(y >> 1) * NH : nullptr;
+    constexpr int RL = PF::R(0), NBL = N / RL, PERL = PF::per(0);
 #pragma unroll
     for (int t = 0; t < PERL; ++t) {
-      const int b = lane + 32 * t;
-      if (NBL % 32 == 0 || b < NBL) {
+      const int u = lane + 32 * t;
+      if ((ROWS * NBL) % 32 == 0 || u < ROWS * NBL) {
+        const int y = y0 + u / NBL, b = u % NBL;
+        const float2* trow = t_slice + (int64_t)y * N;
+        const bool store = store_mode != 0 && (y & 1) == 0 && wave < s_waves;
+        float2* srow = store ? S + wave * s_stride + (int64_t)(y >> 1) * NH : nullptr;
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
           const int x = b + q * NBL;
@@ -87,14 +91,15 @@ k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
   }
   if (!fft_out) return;
   __syncwarp();
-  reg_fft<N, false, false>(v, sbuf, tw, lane);
+  reg_fft<N, false, false>(v, sbuf, LDR, tw, lane);
   {
-    constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = (NBF + 31) / 32;
-    float2* dst = Phi + (wave * N + y) * NH;
+    constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = PF::per(PF::NS - 1);
 #pragma unroll
     for (int t = 0; t < PERF; ++t) {
-      const int b = lane + 32 * t;
-      if (NBF % 32 == 0 || b < NBF) {
+      const int u = lane + 32 * t;
+      if ((ROWS * NBF) % 32 == 0 || u < ROWS * NBF) {
+        const int b = u % NBF;
+        float2* dst = Phi + (wave * N + y0 + u / NBF) * NH;
 #pragma unroll
         for (int q = 0; q < RF; ++q) {
           if (q * NBF < NQ || q * NBF >= N - NQ) {
@@ -107,6 +112,21 @@ k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
   }
 }
 
+// Padding period of the column tile: the forward transform's first stage reads
+// x[b + q N/R0] from it and the inverse transform's last stage writes the same form.
+template <int N>
+__host__ __device__ constexpr int tile_pad() {
+  return plan2_radix(N, 0) > 0 ? N / plan_radix(N, 0) : 8;
+}
+
+template <int N>
+__host__ __device__ constexpr int col_ld() {
+  // tile column stride: the cooperative tile load / store touches 8*ROWS columns of
+  // one row per half-warp; an odd number of float2 words per column keeps it
+  // conflict-free for 16 columns, 2 mod 16 for 8
+  return spad_len(N) + (rows_per_warp(N) == 2 ? 1 : 2);
+}
+
 template <int N>
 __global__ void __launch_bounds__(kColCB * 32)
 k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
@@ -114,49 +134,55 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
            const uint8_t* __restrict__ det_mask, const int* __restrict__ wave_out,
            double* __restrict__ det_acc, double det_scale, const float2* __restrict__ tw) {
   constexpr int NH = N / 2, NQ = N / 4;
-  constexpr int LD = spad_len(N) + 2;   // column stride: keeps the tile load conflict-free
+  constexpr int ROWS = RegFFT<N>::ROWS;
+  constexpr int CB = kColCB * ROWS;          // columns per CTA
+  constexpr int LD = col_ld<N>();
+  constexpr int TP = tile_pad<N>();
   using PI = Plan<N, true>;
   using PF = Plan<N, false>;
   constexpr int E = RegFFT<N>::E;
   extern __shared__ float2 smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kx0 = blockIdx.x * kColCB;
+  const int kx0 = blockIdx.x * CB;
   const int64_t wave = blockIdx.y;
   const float2* src = Phi + wave * (int64_t)N * NH;
   {
-    const int c = threadIdx.x % kColCB;
+    const int c = threadIdx.x % CB;
 #pragma unroll 4
-    for (int r = threadIdx.x / kColCB; r < N; r += 32)
-      smem[c * LD + spad(r)] = src[(int64_t)r * NH + kx0 + c];
+    for (int r = threadIdx.x / CB; r < N; r += (kColCB * 32) / CB)
+      smem[c * LD + spad<TP>(r)] = src[(int64_t)r * NH + kx0 + c];
   }
   __syncthreads();
-  float2* sbuf = smem + warp * LD;
-  const int kx = kx0 + warp;
+  float2* sbuf = smem + warp * ROWS * LD;    // this warp's ROWS columns
   float2 v[E];
   {
-    constexpr int R0 = PF::R(0), NB0 = N / R0, PER0 = (NB0 + 31) / 32;
+    constexpr int R0 = PF::R(0), NB0 = N / R0, PER0 = PF::per(0);
 #pragma unroll
     for (int t = 0; t < PER0; ++t) {
-      const int b = lane + 32 * t;
-      if (NB0 % 32 == 0 || b < NB0) {
+      const int u = lane + 32 * t;
+      if ((ROWS * NB0) % 32 == 0 || u < ROWS * NB0) {
+        const int b = u % NB0;
+        const float2* col = sbuf + (u / NB0) * LD;
 #pragma unroll
-        for (int q = 0; q < R0; ++q) v[t * R0 + q] = sbuf[spad(b + q * NB0)];
+        for (int q = 0; q < R0; ++q) v[t * R0 + q] = col[spad<TP>(b + q * NB0)];
       }
     }
   }
   __syncwarp();
-  reg_fft<N, false, false>(v, sbuf, tw, lane);
-  // y-spectrum in registers at ky = b + q N/RF: keep the box, multiply by the propagator
-  constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = (NBF + 31) / 32;
-  const float2* prow = ptab + (int64_t)kx * NH;
+  reg_fft<N, false, false>(v, sbuf, LD, tw, lane);
+  // y-spectrum: slot u holds ky = u%NBF + q N/RF of column kx0 + warp*ROWS + u/NBF
+  constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = PF::per(PF::NS - 1);
   if (mode == 0) {
 #pragma unroll
     for (int t = 0; t < PERF; ++t) {
-      const int b = lane + 32 * t;
+      const int u = lane + 32 * t;
+      const bool live = (ROWS * NBF) % 32 == 0 || u < ROWS * NBF;
+      const int b = u % NBF;
+      const float2* prow = ptab + (int64_t)(kx0 + warp * ROWS + u / NBF) * NH;
 #pragma unroll
       for (int q = 0; q < RF; ++q) {
         float2 val = make_float2(0.f, 0.f);
-        if ((NBF % 32 == 0 || b < NBF) && (q * NBF < NQ || q * NBF >= N - NQ)) {
+        if (live && (q * NBF < NQ || q * NBF >= N - NQ)) {
           const int pos = b + q * NBF;
           const float2 p = prow[pos < NQ ? pos : pos - NH];
           val = conj_p ? cmulc(v[t * RF + q], p) : cmul(v[t * RF + q], p);
@@ -165,35 +191,41 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
       }
     }
     __syncwarp();
-    reg_fft<N, true, true>(v, sbuf, tw, lane);
+    reg_fft<N, true, true>(v, sbuf, LD, tw, lane);
     {
-      constexpr int RL = PI::R(PI::NS - 1), NBL = N / RL, PERL = (NBL + 31) / 32;
+      constexpr int RL = PI::R(PI::NS - 1), NBL = N / RL, PERL = PI::per(PI::NS - 1);
 #pragma unroll
       for (int t = 0; t < PERL; ++t) {
-        const int b = lane + 32 * t;
-        if (NBL % 32 == 0 || b < NBL) {
+        const int u = lane + 32 * t;
+        if ((ROWS * NBL) % 32 == 0 || u < ROWS * NBL) {
+          const int b = u % NBL;
+          float2* col = sbuf + (u / NBL) * LD;
 #pragma unroll
-          for (int q = 0; q < RL; ++q) sbuf[spad(b + q * NBL)] = v[t * RL + q];
+          for (int q = 0; q < RL; ++q) col[spad<TP>(b + q * NBL)] = v[t * RL + q];
         }
       }
     }
     __syncthreads();
     float2* dst = W + wave * (int64_t)N * NH;
-    const int c = threadIdx.x % kColCB;
+    const int c = threadIdx.x % CB;
 #pragma unroll 4
-    for (int r = threadIdx.x / kColCB; r < N; r += 32)
-      dst[(int64_t)r * NH + kx0 + c] = smem[c * LD + spad(r)];
+    for (int r = threadIdx.x / CB; r < N; r += (kColCB * 32) / CB)
+      dst[(int64_t)r * NH + kx0 + c] = smem[c * LD + spad<TP>(r)];
   } else {
     const int out = wave_out[wave];
     if (out < 0) return;
     float acc = 0.f;
-    const uint8_t* mrow = det_mask + (int64_t)kx * NH;
 #pragma unroll
     for (int t = 0; t < PERF; ++t) {
-      const int b = lane + 32 * t;
+      const int u = lane + 32 * t;
+      const bool live = (ROWS * NBF) % 32 == 0 || u < ROWS * NBF;
+      const int b = u % NBF;
+      const int kx = kx0 + warp * ROWS + u / NBF;
+      const float2* prow = ptab + (int64_t)kx * NH;
+      const uint8_t* mrow = det_mask + (int64_t)kx * NH;
 #pragma unroll
       for (int q = 0; q < RF; ++q) {
-        if ((NBF % 32 == 0 || b < NBF) && (q * NBF < NQ || q * NBF >= N - NQ)) {
+        if (live && (q * NBF < NQ || q * NBF >= N - NQ)) {
           const int pos = b + q * NBF;
           const int ky = pos < NQ ? pos : pos - NH;
           if (mrow[ky]) {
@@ -350,11 +382,12 @@ template <int N>
 cudaError_t row_pass_n(int n_waves, const float2* W, float2* Phi, const float2* t, int conj_t,
                        int store_mode, float2* S, int s_waves, int64_t s_stride, int fft_out,
                        const float2* tw, cudaStream_t s) {
-  const size_t smem = (size_t)kRowWarps * spad_len(N) * sizeof(float2);
+  constexpr int ROWS = RegFFT<N>::ROWS;
+  const size_t smem = (size_t)kRowWarps * ROWS * spad_len(N) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_row_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(N / kRowWarps, n_waves);
+  dim3 grid(N / (kRowWarps * ROWS), n_waves);
   k_row_pass<N><<<grid, kRowWarps * 32, smem, s>>>(W, Phi, t, conj_t, store_mode, S, s_waves,
                                                    s_stride, fft_out, tw);
   return cudaGetLastError();
@@ -364,11 +397,12 @@ template <int N>
 cudaError_t col_pass_n(int n_waves, const float2* Phi, float2* W, const float2* ptab, int conj_p,
                        int mode, const uint8_t* det_mask, const int* wave_out, double* det_acc,
                        double det_scale, const float2* tw, cudaStream_t s) {
-  const size_t smem = (size_t)kColCB * (spad_len(N) + 2) * sizeof(float2);
+  constexpr int ROWS = RegFFT<N>::ROWS;
+  const size_t smem = (size_t)kColCB * ROWS * col_ld<N>() * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_col_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(N / 2 / kColCB, n_waves);
+  dim3 grid(N / 2 / (kColCB * ROWS), n_waves);
   k_col_pass<N><<<grid, kColCB * 32, smem, s>>>(Phi, W, ptab, conj_p, mode, det_mask, wave_out,
                                                 det_acc, det_scale, tw);
   return cudaGetLastError();
