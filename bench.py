@@ -281,6 +281,17 @@ def gpu_arm(args, rank, world):
     h2d = wl.vproj.nbytes + wl.H.nbytes + wl.n_sites * (3 * 4 + 2 * 8)
     d2h = wl.n_types * wl.n_scan * 8
 
+    # accuracy of the timed precision against the FP32 CUDA-core path on the same
+    # workload (the FP32 path is pinned to the FP64 oracle by the parity tests)
+    acc = None
+    if rank == 0 and args.precision != "fp32" and not args.no_eps:
+        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
+        ref = g.inelastic_map_for(ctx, sm, wl, precision="fp32", H=Hdev, stream=stream)
+        sm.free()
+        got = mdev.cpu().numpy()
+        acc = {"eps_vs_fp32_path": float(np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))),
+               "max_abs_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
+
     # quadratic algorithm on the same GPU, seeded probe sample, scaled per pixel-slice
     quad = None
     if rank == 0 and not args.no_quadratic:
@@ -353,6 +364,7 @@ def gpu_arm(args, rank, world):
         "kernels": share,
         "clocks": clk,
         "gpu_quadratic": quad,
+        "accuracy": acc,
     }
     return line
 
@@ -429,6 +441,7 @@ def main():
     ap.add_argument("--quad-probes", type=int, default=8)
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")
     ap.add_argument("--max-slices", type=int, default=0,
                     help="keep only the first K slices (smaller device footprint for profiling)")
     args = ap.parse_args()

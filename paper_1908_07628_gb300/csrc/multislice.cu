@@ -147,10 +147,14 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
   const int64_t wave = blockIdx.y;
   const float2* src = Phi + wave * (int64_t)N * NH;
   {
+    // all N / (256 / CB) loads of a thread in flight at once
     const int c = threadIdx.x % CB;
-#pragma unroll 4
-    for (int r = threadIdx.x / CB; r < N; r += (kColCB * 32) / CB)
-      smem[c * LD + spad<TP>(r)] = src[(int64_t)r * NH + kx0 + c];
+    constexpr int STEP = (kColCB * 32) / CB, NL = N / STEP;
+    float2 tmp[NL];
+#pragma unroll
+    for (int i = 0; i < NL; ++i) tmp[i] = src[(int64_t)(threadIdx.x / CB + i * STEP) * NH + kx0 + c];
+#pragma unroll
+    for (int i = 0; i < NL; ++i) smem[c * LD + spad<TP>(threadIdx.x / CB + i * STEP)] = tmp[i];
   }
   __syncthreads();
   float2* sbuf = smem + warp * ROWS * LD;    // this warp's ROWS columns
@@ -208,9 +212,12 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
     __syncthreads();
     float2* dst = W + wave * (int64_t)N * NH;
     const int c = threadIdx.x % CB;
-#pragma unroll 4
-    for (int r = threadIdx.x / CB; r < N; r += (kColCB * 32) / CB)
+    constexpr int STEP = (kColCB * 32) / CB, NL = N / STEP;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+      const int r = threadIdx.x / CB + i * STEP;
       dst[(int64_t)r * NH + kx0 + c] = smem[c * LD + spad<TP>(r)];
+    }
   } else {
     const int out = wave_out[wave];
     if (out < 0) return;
