@@ -329,6 +329,15 @@ def gpu_arm(args, rank, world):
                     "traffic": measured_traffic(dom, wl.n, waves),
                     "algorithmic_bytes": alg[dom][1],
                     "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+        elif "bf16x3" in dom:
+            useful = contraction_flops(wl, n_in, n_out, dom)
+            # the tensor pipe runs three BF16 products per real product (hi*hi, hi*lo, lo*hi)
+            peak = peaks["bf16_tflops_sustained"]
+            achieved = 3 * useful / per_step / avg_s / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "useful_tflops": useful / per_step / avg_s / 1e12,
+                    "peak_source": "measured bf16 sustained"}
         elif "tf32" in dom:
             flops = contraction_flops(wl, n_in, n_out, dom)
             # TF32 dense = 1.1 / 2.25 of BF16 (nominal); the kernel runs inside a long step
@@ -351,7 +360,7 @@ def gpu_arm(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "tf32" if args.precision == "tf32" else "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"tf32": "tf32", "bf16x3": "bf16x3"}.get(args.precision, "f32"), "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "n_in": n_in,
                    "n_out": n_out, "scan": [wl.scan[0], wl.scan[1]], "n_types": wl.n_types,
                    "precision": args.precision, "parallelism": f"replicas{world}",

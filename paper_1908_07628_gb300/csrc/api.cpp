@@ -433,9 +433,11 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
   eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
   if (r != EELS_OK) return r;
-  if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32)
+  if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32 &&
+      precision != EELS_PREC_BF16X3)
     return fail(ctx, EELS_ERR_UNSUPPORTED, "precision not built");
-  const bool tc = precision == EELS_PREC_TF32;
+  const bool tc = precision != EELS_PREC_FP32;
+  const int tc_prec = precision == EELS_PREC_BF16X3 ? EELS_TC_BF16X3 : EELS_TC_TF32;
   if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
   EELS_CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -531,7 +533,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
 
   // tensor-core path: sites of a slice in batches of `sb` slots
   auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
-  const int k1p = (int)rup(2 * (int64_t)w * w, 32), k2p = (int)rup(2 * (int64_t)n_in, 32);
+  const int kal = eels::tc_k_align(tc_prec);
+  const int k1p = (int)rup(2 * (int64_t)w * w, kal), k2p = (int)rup(2 * (int64_t)n_in, kal);
   const int nr_cap = std::max(L.max_nr, 1);
   const int64_t per_site = 4 * ((int64_t)n_out * k1p + (int64_t)T * 2 * n_in * k1p +
                                 (int64_t)T * n_out * k2p + (int64_t)2 * nr_cap * k2p);
@@ -593,6 +596,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     for (int q0 = site_off[i]; tc && q0 < site_off[i + 1]; q0 += sb) {
       const int ns = std::min(sb, site_off[i + 1] - q0);
       eels::TcBatch b{};
+      b.prec = tc_prec;
       b.Sout = Sout.p; b.Sin = Sin; b.nh = nh; b.n_out = n_out; b.n_in = n_in; b.w = w;
       b.n_types = T; b.H = H; b.wx = dwx.p; b.wy = dwy.p;
       b.slot_site = dslot.p + q0; b.z_site = dzs.p + (int64_t)q0 * T;
@@ -609,11 +613,11 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         EELS_CK(eels::tc_gather(b, st));
       }
       {
-        Prof pr(ctx, "gemm1_tf32", st);
+        Prof pr(ctx, tc_prec == EELS_TC_BF16X3 ? "gemm1_bf16x3" : "gemm1_tf32", st);
         EELS_CK(eels::tc_gemm1(b, st));
       }
       {
-        Prof pr(ctx, "gemm2_abs2_tf32", st);
+        Prof pr(ctx, tc_prec == EELS_TC_BF16X3 ? "gemm2_abs2_bf16x3" : "gemm2_abs2_tf32", st);
         EELS_CK(eels::tc_gemm2(b, st));
       }
     }

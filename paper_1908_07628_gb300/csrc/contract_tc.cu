@@ -1,5 +1,5 @@
-// Inelastic contraction on the tcgen05 tensor cores (TF32 operands, FP32
-// accumulation in TMEM), Eq. SHn0 and the |.|^2 scan sum of Sec. III.
+// Inelastic contraction on the tcgen05 tensor cores with FP32 accumulation in
+// TMEM, Eq. SHn0 and the |.|^2 scan sum of Sec. III.
 //
 // Both complex products are run as real GEMMs with K-major operands whose K
 // axis interleaves (re, im):
@@ -10,10 +10,17 @@
 //   GEMM 2  C2[d][2r+c] = sum_k M[d][k] B2[2r+c][k]
 //           B2[2r]   = conj(a_r),  B2[2r+1] = i conj(a_r)  -> C2 = (Re, Im) of V[d][r]
 //           map[type][R_r] += sum_d C2[d][2r]^2 + C2[d][2r+1]^2     (fused epilogue)
-// Operands are gathered into K-padded buffers (rounded to TF32 nearest) and
-// streamed by TMA (128-byte swizzle) through a 4-stage mbarrier pipeline.  One
-// 128 x 256 tile per CTA: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMA,
-// all four warps drain TMEM in the epilogue.
+//
+// Two operand precisions:
+//   TF32    every operand rounded to the nearest TF32; kind::tf32 MMAs.
+//   BF16x3  every operand x stored as hi = bf16(x) and lo = bf16(x - hi) (two
+//           planes); each product is lo*hi + hi*lo + hi*hi with kind::f16 MMAs into
+//           the same FP32 accumulator (the lo*lo term is below FP32 resolution).
+// Operands are gathered into K-padded buffers [batch][plane][rows][K] and streamed
+// by TMA (128-byte swizzle) through an mbarrier pipeline.  One 128 x 256 tile per
+// CTA: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMA, all four warps drain
+// TMEM in the epilogue.
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -24,16 +31,58 @@ namespace eels {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 4;
-constexpr int B_BYTES = BN * BK * 4;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t IDESC = tc::idesc_tf32(BM, BN);
-constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128, BN = 256;
+
+template <int PREC>
+struct Prec;
+template <>
+struct Prec<EELS_TC_TF32> {
+  using T = float;
+  static constexpr int BK = 32;         // 128 bytes of K per row
+  static constexpr int PLANES = 1;
+  static constexpr int STAGES = 4;
+  static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  static constexpr uint32_t IDESC = tc::idesc_tf32(BM, BN);
+};
+template <>
+struct Prec<EELS_TC_BF16X3> {
+  using T = __nv_bfloat16;
+  static constexpr int BK = 64;
+  static constexpr int PLANES = 2;      // hi, lo
+  static constexpr int STAGES = 2;
+  static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  static constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
+};
+
+template <int PREC>
+struct Tile {
+  using P = Prec<PREC>;
+  static constexpr int A_BYTES = BM * P::BK * (int)sizeof(typename P::T);   // one plane
+  static constexpr int B_BYTES = BN * P::BK * (int)sizeof(typename P::T);
+  static constexpr int STAGE_BYTES = P::PLANES * (A_BYTES + B_BYTES);
+  static constexpr size_t SMEM = (size_t)P::STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// store the pair (a, b) at element e of a row, in every plane of the precision
+template <int PREC>
+__device__ __forceinline__ void put2(void* base, int64_t plane_stride, int64_t e, float a, float b) {
+  if constexpr (PREC == EELS_TC_TF32) {
+    reinterpret_cast<float2*>(static_cast<float*>(base) + e)[0] =
+        make_float2(tc::to_tf32(a), tc::to_tf32(b));
+  } else {
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+    const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+    const __nv_bfloat16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
+    const __nv_bfloat16 bl = __float2bfloat16_rn(b - __bfloat162float(bh));
+    reinterpret_cast<__nv_bfloat162*>(p + e)[0] = __halves2bfloat162(ah, bh);
+    reinterpret_cast<__nv_bfloat162*>(p + plane_stride + e)[0] = __halves2bfloat162(al, bl);
+  }
+}
 
 struct EpiStore {
-  float* out;
-  int64_t z_stride;
+  void* out;
+  int64_t z_stride;      // elements between problems
+  int64_t plane_stride;  // elements between hi and lo planes
   int64_t row_pitch;
   int rows;
   int cols;
@@ -52,11 +101,14 @@ struct EpiAbs2 {
   int rows;
 };
 
-template <int MODE>
+template <int MODE, int PREC>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           int kblocks, const int* __restrict__ a_batch, const int* __restrict__ b_batch,
           const int* __restrict__ n_valid, EpiStore es, EpiAbs2 ea, int* __restrict__ status) {
+  using P = Prec<PREC>;
+  using TL = Tile<PREC>;
+  constexpr int STAGES = P::STAGES, BK = P::BK, PL = P::PLANES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ float red[BN / 2];
   const int z = blockIdx.z;
@@ -65,7 +117,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (n0 >= nv) return;
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * TL::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
@@ -90,27 +142,43 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const uint32_t tmem = *tmem_holder;
   bool ok = true;
 
+  // stage layout: A plane 0 .. PL-1, then B plane 0 .. PL-1 (each 1024-byte aligned)
   if (warp == 0 && lane == 0) {
     const int ab = a_batch[z], bb = b_batch[z];
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb % STAGES;
       if (kb >= STAGES) ok &= tc::mbar_wait(empty + s, ((kb / STAGES) - 1) & 1);
-      uint8_t* sa = sm + s * STAGE_BYTES;
-      tc::mbar_arrive_expect_tx(full + s, STAGE_BYTES);
-      tc::tma_load_3d(sa, &ta, full + s, kb * BK, m0, ab);
-      tc::tma_load_3d(sa + A_BYTES, &tb, full + s, kb * BK, n0, bb);
+      uint8_t* st = sm + s * TL::STAGE_BYTES;
+      tc::mbar_arrive_expect_tx(full + s, TL::STAGE_BYTES);
+#pragma unroll
+      for (int pl = 0; pl < PL; ++pl) {
+        tc::tma_load_4d(st + pl * TL::A_BYTES, &ta, full + s, kb * BK, m0, pl, ab);
+        tc::tma_load_4d(st + PL * TL::A_BYTES + pl * TL::B_BYTES, &tb, full + s, kb * BK, n0, pl,
+                        bb);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb % STAGES;
       ok &= tc::mbar_wait(full + s, (kb / STAGES) & 1);
       tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(sm + s * STAGE_BYTES);
-      const uint32_t sb = sa + A_BYTES;
+      const uint32_t sa = tc::smem_u32(sm + s * TL::STAGE_BYTES);
+      const uint32_t sb = sa + PL * TL::A_BYTES;
+      // each MMA consumes 32 bytes of K: 8 TF32 or 16 BF16 elements
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk)
-        tc::mma_tf32(tmem, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32), IDESC,
-                     (kb | kk) != 0 ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+        if constexpr (PREC == EELS_TC_TF32) {
+          tc::mma_tf32(tmem, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32), P::IDESC,
+                       acc);
+        } else {
+          const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
+          const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
+          tc::mma_f16(tmem, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
+          tc::mma_f16(tmem, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
+          tc::mma_f16(tmem, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
+        }
+      }
       tc::mma_commit(empty + s);
     }
     tc::mma_commit(done);
@@ -122,17 +190,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const int row = m0 + warp * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   if constexpr (MODE == 0) {
-    float* dst = es.out + (int64_t)z * es.z_stride + (int64_t)row * es.row_pitch;
+    const int64_t rbase = (int64_t)z * es.z_stride + (int64_t)row * es.row_pitch;
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tc::tmem_ld16(trow + c, v);
       const int col = n0 + c;
       if (row < es.rows && col < es.cols) {
-        float4* d4 = reinterpret_cast<float4*>(dst + col);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          d4[q] = make_float4(tc::to_tf32(v[4 * q]), tc::to_tf32(v[4 * q + 1]),
-                              tc::to_tf32(v[4 * q + 2]), tc::to_tf32(v[4 * q + 3]));
+        for (int q = 0; q < 8; ++q)
+          put2<PREC>(es.out, es.plane_stride, rbase + col + 2 * q, v[2 * q], v[2 * q + 1]);
       }
     }
   } else {
@@ -184,14 +250,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (!ok && status) atomicExch(status, 1);
 }
 
-// A1[slot][d][2p + c] = tf32(Sout[d][pixel p of the window of site slot_site[slot]])
+// A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]]
+template <int PREC>
 __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out, int w,
                               const int* __restrict__ slot_site, const int* __restrict__ wx,
-                              const int* __restrict__ wy, float* __restrict__ A1, int k1p) {
+                              const int* __restrict__ wy, void* __restrict__ A1, int k1p) {
+  constexpr int PL = Prec<PREC>::PLANES;
   const int d = blockIdx.x, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int64_t plane = (int64_t)nh * nh;
-  float2* row = reinterpret_cast<float2*>(A1 + ((int64_t)slot * n_out + d) * k1p);
+  const int64_t pstride = (int64_t)n_out * k1p;
+  const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d * k1p;
   const float2* src = Sout + (int64_t)d * plane;
   const int P = w * w;
   for (int p = threadIdx.x; p < k1p / 2; p += blockDim.x) {
@@ -200,22 +269,25 @@ __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out
       const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
       v = src[(int64_t)gy * nh + gx];
     }
-    row[p] = make_float2(tc::to_tf32(v.x), tc::to_tf32(v.y));
+    put2<PREC>(A1, pstride, rbase + 2 * p, v.x, v.y);
   }
 }
 
-// B1[z][2j][2p + c] = tf32(H_z[p] Sin[j][p]),  B1[z][2j+1] = tf32(-i H_z[p] Sin[j][p])
+// B1[z][plane][2j][2p + c] = H_z[p] Sin[j][p],  B1[z][plane][2j+1] = -i H_z[p] Sin[j][p]
+template <int PREC>
 __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in, int w,
                                const int* __restrict__ z_site, const int* __restrict__ z_type,
                                const float2* __restrict__ H, int n_types,
                                const int* __restrict__ wx, const int* __restrict__ wy,
-                               float* __restrict__ B1, int k1p) {
+                               void* __restrict__ B1, int k1p) {
+  constexpr int PL = Prec<PREC>::PLANES;
   const int j = blockIdx.x, z = blockIdx.y;
   const int s = z_site[z];
   const int64_t plane = (int64_t)nh * nh;
+  const int64_t pstride = (int64_t)2 * n_in * k1p;
+  const int64_t r0 = (int64_t)z * PL * pstride + (int64_t)(2 * j) * k1p;
+  const int64_t r1 = r0 + k1p;
   const float2* Hz = H + ((int64_t)s * n_types + z_type[z]) * w * w;
-  float2* r0 = reinterpret_cast<float2*>(B1 + ((int64_t)z * 2 * n_in + 2 * j) * k1p);
-  float2* r1 = r0 + k1p / 2;
   const float2* src = Sin + (int64_t)j * plane;
   const int P = w * w;
   for (int p = threadIdx.x; p < k1p / 2; p += blockDim.x) {
@@ -224,23 +296,27 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
       const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
       v = cmul(Hz[p], src[(int64_t)gy * nh + gx]);
     }
-    r0[p] = make_float2(tc::to_tf32(v.x), tc::to_tf32(v.y));
-    r1[p] = make_float2(tc::to_tf32(v.y), tc::to_tf32(-v.x));
+    put2<PREC>(B1, pstride, r0 + 2 * p, v.x, v.y);
+    put2<PREC>(B1, pstride, r1 + 2 * p, v.y, -v.x);
   }
 }
 
-// B2[slot][2r] = conj(a_r), B2[slot][2r+1] = i conj(a_r), a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
+// B2[slot][plane][2r] = conj(a_r), B2[slot][plane][2r+1] = i conj(a_r),
+// a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
+template <int PREC>
 __global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __restrict__ ay,
                                int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
                                const int* __restrict__ xoff, const int* __restrict__ xcnt,
                                const int* __restrict__ xlist, const int* __restrict__ yoff,
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
-                               int nr_cap, float* __restrict__ B2, int k2p) {
+                               int nr_cap, void* __restrict__ B2, int k2p) {
+  constexpr int PL = Prec<PREC>::PLANES;
   const int r = blockIdx.x, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
-  float2* r0 = reinterpret_cast<float2*>(B2 + ((int64_t)slot * 2 * nr_cap + 2 * r) * k2p);
-  float2* r1 = r0 + k2p / 2;
+  const int64_t pstride = (int64_t)2 * nr_cap * k2p;
+  const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)(2 * r) * k2p;
+  const int64_t r1 = r0 + k2p;
   int ix = 0, iy = 0;
   if (r < nr) {
     ix = xlist[xoff[s] + r % nx];
@@ -249,8 +325,8 @@ __global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __re
   for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
     float2 a = make_float2(0.f, 0.f);
     if (r < nr && j < n_in) a = cmul(ax[(int64_t)j * n_sx + ix], ay[(int64_t)j * n_sy + iy]);
-    r0[j] = make_float2(tc::to_tf32(a.x), tc::to_tf32(-a.y));
-    r1[j] = make_float2(tc::to_tf32(a.y), tc::to_tf32(a.x));
+    put2<PREC>(B2, pstride, r0 + 2 * j, a.x, -a.y);
+    put2<PREC>(B2, pstride, r1 + 2 * j, a.y, a.x);
   }
 }
 
@@ -267,84 +343,117 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3D FP32 tensor map (k, rows, batch), K-major rows of k elements, box (32, box_rows, 1),
+// 4D tensor map (k, rows, plane, batch) over a K-major buffer; box (BK, box_rows, 1, 1),
 // 128-byte swizzle; out-of-range rows read as zero.
-cudaError_t make_map(CUtensorMap* map, float* base, int k, int rows, int batch, int box_rows) {
+template <int PREC>
+cudaError_t make_map(CUtensorMap* map, void* base, int k, int rows, int batch, int box_rows) {
+  using P = Prec<PREC>;
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)batch};
-  cuuint64_t strides[2] = {(cuuint64_t)k * 4, (cuuint64_t)k * 4 * (cuuint64_t)rows};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const cuuint64_t es = sizeof(typename P::T);
+  cuuint64_t dims[4] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)P::PLANES, (cuuint64_t)batch};
+  cuuint64_t strides[3] = {(cuuint64_t)k * es, (cuuint64_t)k * es * rows,
+                           (cuuint64_t)k * es * rows * P::PLANES};
+  cuuint32_t box[4] = {(cuuint32_t)P::BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, P::DT, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-}  // namespace
+template <int PREC>
+cudaError_t set_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const int smem = (int)Tile<PREC>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0, PREC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tc_gemm<1, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
 
-cudaError_t tc_gather(const TcBatch& b, cudaStream_t st) {
-  if (b.n_sites <= 0) return cudaSuccess;
+template <int PREC>
+cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
   const int nz = b.n_sites * b.n_types;
   cudaError_t e;
-  k_gather_sout<<<dim3(b.n_out, b.n_sites), 256, 0, st>>>(b.Sout, b.nh, b.n_out, b.w, b.slot_site,
-                                                           b.wx, b.wy, b.A1, b.k1p);
+  k_gather_sout<PREC><<<dim3(b.n_out, b.n_sites), 256, 0, st>>>(b.Sout, b.nh, b.n_out, b.w,
+                                                                 b.slot_site, b.wx, b.wy, b.A1,
+                                                                 b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_gather_sin_h<<<dim3(b.n_in, nz), 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.z_site, b.z_type,
-                                                    b.H, b.n_types, b.wx, b.wy, b.B1, b.k1p);
+  k_gather_sin_h<PREC><<<dim3(b.n_in, nz), 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.z_site,
+                                                          b.z_type, b.H, b.n_types, b.wx, b.wy,
+                                                          b.B1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_gather_probe<<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
+  k_gather_probe<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
       b.ax, b.ay, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt,
       b.ylist, b.nr_cap, b.B2, b.k2p);
   return cudaGetLastError();
 }
 
-namespace {
-cudaError_t set_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)GEMM_SMEM);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)GEMM_SMEM);
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-}  // namespace
-
-cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t st) {
-  if (b.n_sites <= 0) return cudaSuccess;
+template <int PREC>
+cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs()) != cudaSuccess) return e;
+  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mA1, mB1;
-  if ((e = make_map(&mA1, b.A1, b.k1p, b.n_out, b.slots_cap, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&mB1, b.B1, b.k1p, 2 * b.n_in, b.slots_cap * b.n_types, BN)) != cudaSuccess)
+  if ((e = make_map<PREC>(&mA1, b.A1, b.k1p, b.n_out, b.slots_cap, BM)) != cudaSuccess) return e;
+  if ((e = make_map<PREC>(&mB1, b.B1, b.k1p, 2 * b.n_in, b.slots_cap * b.n_types, BN)) !=
+      cudaSuccess)
     return e;
-  EpiStore es{b.M1, (int64_t)b.n_out * b.k2p, b.k2p, b.n_out, b.k2p};
+  const int64_t pstride = (int64_t)b.n_out * b.k2p;
+  EpiStore es{b.M1, Prec<PREC>::PLANES * pstride, pstride, b.k2p, b.n_out, b.k2p};
   EpiAbs2 ea{};
   dim3 g1((b.k2p + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<0><<<g1, 128, GEMM_SMEM, st>>>(mA1, mB1, b.k1p / BK, b.a_batch1, b.b_batch1,
-                                            b.n_valid1, es, ea, b.status);
+  k_tc_gemm<0, PREC><<<g1, 128, Tile<PREC>::SMEM, st>>>(mA1, mB1, b.k1p / Prec<PREC>::BK,
+                                                         b.a_batch1, b.b_batch1, b.n_valid1, es,
+                                                         ea, b.status);
   return cudaGetLastError();
 }
 
-cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t st) {
-  if (b.n_sites <= 0) return cudaSuccess;
+template <int PREC>
+cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs()) != cudaSuccess) return e;
+  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mM1, mB2;
-  if ((e = make_map(&mM1, b.M1, b.k2p, b.n_out, b.slots_cap * b.n_types, BM)) != cudaSuccess)
+  if ((e = make_map<PREC>(&mM1, b.M1, b.k2p, b.n_out, b.slots_cap * b.n_types, BM)) !=
+      cudaSuccess)
     return e;
-  if ((e = make_map(&mB2, b.B2, b.k2p, 2 * b.nr_cap, b.slots_cap, BN)) != cudaSuccess) return e;
+  if ((e = make_map<PREC>(&mB2, b.B2, b.k2p, 2 * b.nr_cap, b.slots_cap, BN)) != cudaSuccess)
+    return e;
   EpiStore es{};
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   dim3 g2((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<1><<<g2, 128, GEMM_SMEM, st>>>(mM1, mB2, b.k2p / BK, b.a_batch2, b.b_batch2,
-                                            b.n_valid2, es, ea, b.status);
+  k_tc_gemm<1, PREC><<<g2, 128, Tile<PREC>::SMEM, st>>>(mM1, mB2, b.k2p / Prec<PREC>::BK,
+                                                         b.a_batch2, b.b_batch2, b.n_valid2, es,
+                                                         ea, b.status);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_k_align(int prec) {
+  return prec == EELS_TC_BF16X3 ? Prec<EELS_TC_BF16X3>::BK : Prec<EELS_TC_TF32>::BK;
+}
+
+cudaError_t tc_gather(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gather_impl<EELS_TC_BF16X3>(b, st)
+                                  : gather_impl<EELS_TC_TF32>(b, st);
+}
+
+cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gemm1_impl<EELS_TC_BF16X3>(b, st)
+                                  : gemm1_impl<EELS_TC_TF32>(b, st);
+}
+
+cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gemm2_impl<EELS_TC_BF16X3>(b, st)
+                                  : gemm2_impl<EELS_TC_TF32>(b, st);
 }
 
 }  // namespace eels

@@ -81,10 +81,15 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
                                double r0, double step, int n_pos, cudaStream_t s);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
 
-// Tensor-core (tcgen05, TF32) contraction of a batch of sites of one slice:
-// gathers the windowed operands, runs GEMM 1 (M = Sout^H diag(H) Sin) and GEMM 2
-// with the fused sum_d |.|^2 epilogue into map.  All pointers are device memory.
+// Tensor-core (tcgen05) contraction of a batch of sites of one slice: gathers the
+// windowed operands, runs GEMM 1 (M = Sout^H diag(H) Sin) and GEMM 2 with the fused
+// sum_d |.|^2 epilogue into map.  All pointers are device memory.  Operand buffers
+// hold 4 bytes per value in both precisions (one TF32 plane, or BF16 hi + lo planes).
+#define EELS_TC_TF32 0
+#define EELS_TC_BF16X3 1
+int tc_k_align(int prec);   // K padding (elements) of the operand buffers
 struct TcBatch {
+  int prec;                               // EELS_TC_TF32 or EELS_TC_BF16X3
   const float2* Sout; const float2* Sin;  // depth planes [beam][nh][nh]
   int nh, n_out, n_in, w, n_types;
   const float2* H;                        // [S][T][w][w]
@@ -93,7 +98,7 @@ struct TcBatch {
   const int* z_site; const int* z_type;   // [n_sites * T] transition z = slot*T + type
   int n_sites, slots_cap;                 // sites in this batch, buffer capacity in sites
   int k1p, k2p;                           // padded K of GEMM 1 (2 w^2) and GEMM 2 (2 n_in)
-  float* A1; float* B1; float* M1; float* B2;
+  void* A1; void* B1; void* M1; void* B2;
   const float2* ax; const float2* ay; int n_sx, n_sy;
   const int* xoff; const int* xcnt; const int* xlist;
   const int* yoff; const int* ycnt; const int* ylist;

@@ -19,7 +19,9 @@ pytestmark = pytest.mark.gpu
 EPS_FP32 = 1e-4
 # tensor-core path: operands rounded to TF32 (unit roundoff 2^-11), FP32 accumulate
 EPS_TC = 1e-3
-EPS = {"fp32": EPS_FP32, "tf32": EPS_TC}
+# BF16 hi+lo split: each operand carries ~16 significant bits, three products
+EPS = {"fp32": EPS_FP32, "tf32": EPS_TC, "bf16x3": EPS_TC}
+PRECS = ("fp32", "tf32", "bf16x3")
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +78,7 @@ def test_linear_map_matches_oracle(g, ctx, n, f, seed, w):
     ref = lin.linear_map(wl) if n >= 256 else ms.quadratic_map(wl)
     sm = g.build_smatrix_for(ctx, wl)
     assert ref.max() > 0
-    for prec in ("fp32", "tf32"):
+    for prec in PRECS:
         got = g.inelastic_map_for(ctx, sm, wl, prec)
         assert eps(ref, got) < EPS[prec], prec
 
@@ -88,7 +90,7 @@ def test_rocksalt_small_full_map(g, ctx):
     for iy, ix in [(0, 0), (5, 2)]:
         assert np.allclose(q[:, iy, ix], ref[:, iy, ix], rtol=1e-12, atol=0)
     sm = g.build_smatrix_for(ctx, wl)
-    for prec in ("fp32", "tf32"):
+    for prec in PRECS:
         got = g.inelastic_map_for(ctx, sm, wl, prec)
         assert eps(ref, got) < EPS[prec], prec
         for m in range(wl.n_types):
@@ -122,7 +124,7 @@ def test_quadratic_reference_subset_positions(g, ctx):
 def test_no_sites_gives_zero_map(g, ctx):
     wl = _rand(64, 1, 10).with_sites([])
     sm = g.build_smatrix_for(ctx, wl)
-    for prec in ("fp32", "tf32"):
+    for prec in PRECS:
         got = g.inelastic_map_for(ctx, sm, wl, prec)
         assert got.shape == (wl.n_types, wl.scan[1], wl.scan[0]) and not got.any()
 
@@ -132,7 +134,7 @@ def test_single_slice_and_extreme_windows(g, ctx):
         wl = _rand(64, 1, 11 + w, n_z=1, w=w, n_sites=3)
         ref = ms.quadratic_map(wl)
         sm = g.build_smatrix_for(ctx, wl)
-        for prec in ("fp32", "tf32"):
+        for prec in PRECS:
             got = g.inelastic_map_for(ctx, sm, wl, prec)
             assert eps(ref, got) < EPS[prec], (w, prec)
 
@@ -198,7 +200,7 @@ def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
     ref = ms.quadratic_map(sub, positions=pos)
     r = np.array([ref[:, iy, ix] for iy, ix in pos])
     assert r.max() > 0
-    for prec in ("fp32", "tf32"):
+    for prec in PRECS:
         got = g.inelastic_map_for(ctx, sm, sub, prec)
         t = np.array([got[:, iy, ix] for iy, ix in pos])
         assert eps(r, t) < EPS[prec], prec
