@@ -204,3 +204,32 @@ def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
         got = g.inelastic_map_for(ctx, sm, sub, prec)
         t = np.array([got[:, iy, ix] for iy, ix in pos])
         assert eps(r, t) < EPS[prec], prec
+
+
+@pytest.mark.parametrize("name,targets,probes", [
+    ("rocksalt_vacancy", (0, 40, 79), [(16, 16), (2, 29)]),
+    ("nanoparticle", (12, 25, 44), [(64, 64), (60, 70)]),
+])
+def test_large_workloads_sampled(g, ctx, name, targets, probes):
+    """768^2 vacancy crystal (80 slices, f = 2) and 1024^2 nanoparticle (50 slices, f = 4):
+    the full S-matrix, three sites at three depths near the first probe, the m = 0
+    channel; the conventional FP64 oracle evaluates the sampled probes."""
+    wl = sp.WORKLOADS[name]()
+    rx, ry = wl.scan_positions()
+    cx, cy = rx[probes[0][1]], ry[probes[0][0]]
+    chosen = []
+    for target in targets:
+        idx = np.nonzero(wl.site_slice == target)[0]
+        assert idx.size, target
+        d2 = (wl.site_x[idx] - cx) ** 2 + (wl.site_y[idx] - cy) ** 2
+        chosen.append(int(idx[np.argmin(d2)]))
+    sub = wl.with_sites(chosen)
+    sub.H = np.ascontiguousarray(sub.H[:, 1:2])
+    sm = g.build_smatrix_for(ctx, sub)
+    ref = ms.quadratic_map(sub, positions=probes)
+    r = np.array([ref[:, iy, ix] for iy, ix in probes])
+    assert r.max() > 0
+    for prec in PRECS:
+        got = g.inelastic_map_for(ctx, sm, sub, prec)
+        t = np.array([got[:, iy, ix] for iy, ix in probes])
+        assert eps(r, t) < EPS[prec], (prec, eps(r, t))
