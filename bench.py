@@ -400,17 +400,19 @@ def _window_count(s, r, cell, f):
 def contraction_flops(wl, n_in, n_out, kernel):
     """Real flops of the contraction kernels over the whole workload (8 per complex MAC)."""
     rx, ry = wl.scan_positions()
-    g1 = g2 = 0
+    g1 = g2 = gy = gv = 0
+    P = wl.w * wl.w
     for s in range(wl.n_sites):
         nx = _window_count(wl.site_x[s], rx, wl.cell, wl.f)
         ny = _window_count(wl.site_y[s], ry, wl.cell, wl.f)
         if nx and ny:
-            g1 += wl.n_types * n_out * wl.w * wl.w * n_in
-            g2 += wl.n_types * n_out * n_in * nx * ny
-    if "gemm1" in kernel:
-        return 8.0 * g1
-    if "gemm2" in kernel:
-        return 8.0 * g2
+            g1 += wl.n_types * n_out * P * n_in           # M_n = S_out^H diag(H) S_in
+            g2 += wl.n_types * n_out * n_in * nx * ny     # M_n a(R)
+            gy += nx * ny * n_in * P                      # Y = S_in a(R), once per site
+            gv += wl.n_types * n_out * P * nx * ny        # S_out^H (H . Y)
+    for key, val in (("gemm1", g1), ("gemm2", g2), ("gemm_y", gy), ("gemm_v", gv)):
+        if key in kernel:
+            return 8.0 * val
     return 8.0 * (g1 + g2)
 
 

@@ -154,6 +154,21 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
                                          const int32_t* positions, int n_pos, double* map_out,
                                          int map_on_device, void* stream, int64_t* steps);
 
+/* Context options.
+ * EELS_OPT_ASSOCIATION selects how the tensor-core contraction groups the triple
+ * product sum_p conj(S_out[d,p]) H_n[p] sum_j S_in[j,p] a_j(R) (Eq. SHn0 applied to
+ * the probes): EELS_ASSOC_AUTO (default) picks, per call, the grouping with fewer
+ * tensor-core flops over all sites; EELS_ASSOC_TRANSITION_FIRST forms
+ * M_n = S_out^H diag(H_n) S_in and then M_n a(R) (the paper's order);
+ * EELS_ASSOC_PROBE_FIRST forms Y = S_in a(R) once per site (the elastic wave inside the
+ * window) and then S_out^H (H_n . Y) per channel.  Both give the same map up to rounding.
+ * Returns EELS_ERR_ARG for an unknown option or value. */
+#define EELS_OPT_ASSOCIATION 1
+#define EELS_ASSOC_AUTO 0
+#define EELS_ASSOC_TRANSITION_FIRST 1
+#define EELS_ASSOC_PROBE_FIRST 2
+eels_status eels_set_option(eels_ctx* ctx, int option, int value);
+
 /* Per-kernel device timing.  While enabled, every kernel launch made by calls on
  * this context is bracketed by CUDA events recorded on the launch stream.
  * eels_profile_read synchronises those events, folds them into running totals

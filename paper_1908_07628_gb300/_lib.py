@@ -66,6 +66,7 @@ EXPORTS = {
                                                C.POINTER(Transitions), C.POINTER(Scan), C.c_double,
                                                C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                                C.c_void_p, C.POINTER(C.c_int64)]),
+    "eels_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "eels_build_smatrix_static": (C.c_int, [C.POINTER(Specimen), C.POINTER(Optics), C.c_void_p,
@@ -157,6 +158,12 @@ class Context:
         if st != 0:
             msg = self._lib.eels_last_error(self._h)
             raise EelsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    ASSOCIATIONS = {"auto": 0, "transition_first": 1, "probe_first": 2}
+
+    def set_association(self, how: str = "auto"):
+        """Grouping of the tensor-core contraction (EELS_OPT_ASSOCIATION)."""
+        self._check(self._lib.eels_set_option(self._h, 1, self.ASSOCIATIONS[how]), "set_option")
 
     def profile_enable(self, on: bool = True):
         self._check(self._lib.eels_profile_enable(self._h, 1 if on else 0), "profile_enable")

@@ -19,6 +19,9 @@
 
 struct eels_ctx {
   int device = 0;
+  int assoc = EELS_ASSOC_AUTO;
+  // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
+  std::map<std::vector<int64_t>, int> assoc_cache;
   std::string err;
   std::map<int, float2*> tw;   // device twiddle table exp(-2 pi i k/N), by N
   // kernel timing records (eels_profile_enable)
@@ -216,6 +219,17 @@ void eels_destroy(eels_ctx* ctx) {
 }
 
 const char* eels_last_error(const eels_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
+  if (!ctx) return EELS_ERR_ARG;
+  if (option == EELS_OPT_ASSOCIATION) {
+    if (value < EELS_ASSOC_AUTO || value > EELS_ASSOC_PROBE_FIRST)
+      return fail(ctx, EELS_ERR_ARG, "unknown association");
+    ctx->assoc = value;
+    return EELS_OK;
+  }
+  return fail(ctx, EELS_ERR_ARG, "unknown option");
+}
 
 eels_status eels_profile_enable(eels_ctx* ctx, int on) {
   if (!ctx) return EELS_ERR_ARG;
@@ -536,23 +550,40 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   const int kal = eels::tc_k_align(tc_prec);
   const int k1p = (int)rup(2 * (int64_t)w * w, kal), k2p = (int)rup(2 * (int64_t)n_in, kal);
   const int nr_cap = std::max(L.max_nr, 1);
-  const int64_t per_site = 4 * ((int64_t)n_out * k1p + (int64_t)T * 2 * n_in * k1p +
-                                (int64_t)T * n_out * k2p + (int64_t)2 * nr_cap * k2p);
-  int max_sites = 0;
   std::vector<std::vector<int>> slice_sites(n_z);
   for (int s = 0; s < S; ++s)
     if (L.xcnt[s] > 0 && L.ycnt[s] > 0) slice_sites[tr->slice[s]].push_back(s);
+  // AUTO: measured once per shape (both groupings timed on the first occupied slice)
+  const std::vector<int64_t> shape_key = {tc_prec, n, n_out, n_in, w, nr_cap, T};
+  int chosen = ctx->assoc;
+  if (chosen == EELS_ASSOC_AUTO) {
+    auto it = ctx->assoc_cache.find(shape_key);
+    if (it != ctx->assoc_cache.end()) chosen = it->second;
+  }
+  bool tune = tc && chosen == EELS_ASSOC_AUTO;
+  const bool need_tr = tune || chosen == EELS_ASSOC_TRANSITION_FIRST;
+  const bool need_pr = tune || chosen == EELS_ASSOC_PROBE_FIRST;
+  const int64_t per_site =
+      4 * ((int64_t)n_out * k1p +
+           (need_pr ? (int64_t)nr_cap * k2p + (int64_t)k1p * k2p + (int64_t)T * 2 * nr_cap * k1p
+                    : 0) +
+           (need_tr ? (int64_t)T * 2 * n_in * k1p + (int64_t)T * n_out * k2p +
+                          (int64_t)2 * nr_cap * k2p
+                    : 0));
+  int max_sites = 0;
   for (int i = 0; i < n_z; ++i) max_sites = std::max(max_sites, (int)slice_sites[i].size());
   const int sb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(max_sites, 1),
                                                              ((int64_t)3 << 30) / per_site));
-  DevBuf<float> A1, B1, M1, B2;
-  DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus;
-  std::vector<int> slot_all, zs_all, zt_all, nv2_all, site_off(n_z + 1, 0);
+  DevBuf<float> A1, B1, M1, B2, AY, BY, BV;
+  DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus, daby, dnvy, dnry;
+  DevBuf<double> dscratch;
+  std::vector<int> slot_all, zs_all, zt_all, nv2_all, nr_all, site_off(n_z + 1, 0);
   if (tc) {
     for (int i = 0; i < n_z; ++i) {
       site_off[i] = (int)slot_all.size();
       for (int s : slice_sites[i]) {
         slot_all.push_back(s);
+        nr_all.push_back(L.xcnt[s] * L.ycnt[s]);
         for (int m = 0; m < T; ++m) {
           zs_all.push_back(s);
           zt_all.push_back(m);
@@ -575,9 +606,22 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     EELS_CK(dstatus.alloc(1, st));
     EELS_CK(cudaMemsetAsync(dstatus.p, 0, sizeof(int), st));
     EELS_CK(A1.alloc((size_t)sb * n_out * k1p, st));
-    EELS_CK(B1.alloc((size_t)sb * T * 2 * n_in * k1p, st));
-    EELS_CK(M1.alloc((size_t)sb * T * n_out * k2p, st));
-    EELS_CK(B2.alloc((size_t)sb * 2 * nr_cap * k2p, st));
+    if (need_pr) {
+      std::vector<int> aby(sb), nvy(sb, k1p);
+      for (int q = 0; q < sb; ++q) aby[q] = q;
+      EELS_CK(daby.upload(aby.data(), aby.size(), st));
+      EELS_CK(dnvy.upload(nvy.data(), nvy.size(), st));
+      EELS_CK(dnry.upload(nr_all.data(), nr_all.size(), st));
+      EELS_CK(AY.alloc((size_t)sb * nr_cap * k2p, st));
+      EELS_CK(BY.alloc((size_t)sb * k1p * k2p, st));
+      EELS_CK(BV.alloc((size_t)sb * T * 2 * nr_cap * k1p, st));
+    }
+    if (need_tr) {
+      EELS_CK(B1.alloc((size_t)sb * T * 2 * n_in * k1p, st));
+      EELS_CK(M1.alloc((size_t)sb * T * n_out * k2p, st));
+      EELS_CK(B2.alloc((size_t)sb * 2 * nr_cap * k2p, st));
+    }
+    if (tune) EELS_CK(dscratch.alloc((size_t)n_map, st));
   }
 
   {
@@ -585,15 +629,9 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     EELS_CK(eels::launch_init_plane_waves(W.p, n, n_out, dpx.p, dpy.p, damp.p, tw, st));
   }
   eels::WindowLists wl{dxoff.p, dxcnt.p, dxlist.p, dyoff.p, dycnt.p, dylist.p, L.max_nr};
-  for (int i = n_z - 1; i >= 0; --i) {
-    // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
-    {
-      Prof pr(ctx, "row_pass_adjoint", st);
-      EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, sm->t + (int64_t)i * n * n, 1, 2, Sout.p, n_out,
-                              plane, i > 0 ? 1 : 0, tw, st));
-    }
-    const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
-    for (int q0 = site_off[i]; tc && q0 < site_off[i + 1]; q0 += sb) {
+  // tensor-core contraction of slice i with one grouping, accumulated into `map`
+  auto contract_slice = [&](const float2* Sin, int i, int pf, double* map) -> eels_status {
+    for (int q0 = site_off[i]; q0 < site_off[i + 1]; q0 += sb) {
       const int ns = std::min(sb, site_off[i + 1] - q0);
       eels::TcBatch b{};
       b.prec = tc_prec;
@@ -607,18 +645,80 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.yoff = dyoff.p; b.ycnt = dycnt.p; b.ylist = dylist.p; b.nr_cap = nr_cap;
       b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;
       b.a_batch2 = dab2.p; b.b_batch2 = dbb2.p; b.n_valid2 = dnv2.p + (int64_t)q0 * T;
-      b.map = dmap.p; b.status = dstatus.p;
-      {
-        Prof pr(ctx, "tc_gather", st);
-        EELS_CK(eels::tc_gather(b, st));
+      b.map = map; b.status = dstatus.p;
+      b.AY = AY.p; b.BY = BY.p; b.BV = BV.p; b.a_batch_y = daby.p; b.n_valid_y = dnvy.p;
+      b.m_valid_y = dnry.p ? dnry.p + q0 : nullptr;
+      const bool bf = tc_prec == EELS_TC_BF16X3;
+      if (pf) {
+        {
+          Prof pr(ctx, "tc_gather_y", st);
+          EELS_CK(eels::tc_gather_y(b, st));
+        }
+        {
+          Prof pr(ctx, bf ? "gemm_y_bf16x3" : "gemm_y_tf32", st);
+          EELS_CK(eels::tc_gemm_y(b, st));
+        }
+        {
+          Prof pr(ctx, bf ? "gemm_v_abs2_bf16x3" : "gemm_v_abs2_tf32", st);
+          EELS_CK(eels::tc_gemm_v(b, st));
+        }
+      } else {
+        {
+          Prof pr(ctx, "tc_gather", st);
+          EELS_CK(eels::tc_gather(b, st));
+        }
+        {
+          Prof pr(ctx, bf ? "gemm1_bf16x3" : "gemm1_tf32", st);
+          EELS_CK(eels::tc_gemm1(b, st));
+        }
+        {
+          Prof pr(ctx, bf ? "gemm2_abs2_bf16x3" : "gemm2_abs2_tf32", st);
+          EELS_CK(eels::tc_gemm2(b, st));
+        }
       }
-      {
-        Prof pr(ctx, tc_prec == EELS_TC_BF16X3 ? "gemm1_bf16x3" : "gemm1_tf32", st);
-        EELS_CK(eels::tc_gemm1(b, st));
-      }
-      {
-        Prof pr(ctx, tc_prec == EELS_TC_BF16X3 ? "gemm2_abs2_bf16x3" : "gemm2_abs2_tf32", st);
-        EELS_CK(eels::tc_gemm2(b, st));
+    }
+    return EELS_OK;
+  };
+  for (int i = n_z - 1; i >= 0; --i) {
+    // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
+    {
+      Prof pr(ctx, "row_pass_adjoint", st);
+      EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, sm->t + (int64_t)i * n * n, 1, 2, Sout.p, n_out,
+                              plane, i > 0 ? 1 : 0, tw, st));
+    }
+    const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
+    if (tc && site_off[i + 1] > site_off[i]) {
+      int pf = chosen == EELS_ASSOC_PROBE_FIRST ? 1 : 0;
+      if (tune) {
+        // warm both paths on the scratch map, then time each once and keep the faster
+        EELS_CK(cudaMemsetAsync(dscratch.p, 0, sizeof(double) * n_map, st));
+        eels_status r1 = contract_slice(Sin, i, 1, dscratch.p);
+        if (r1 != EELS_OK) return r1;
+        if ((r1 = contract_slice(Sin, i, 0, dscratch.p)) != EELS_OK) return r1;
+        cudaEvent_t e0, e1, e2;
+        EELS_CK(cudaEventCreate(&e0));
+        EELS_CK(cudaEventCreate(&e1));
+        EELS_CK(cudaEventCreate(&e2));
+        EELS_CK(cudaEventRecord(e0, st));
+        if ((r1 = contract_slice(Sin, i, 0, dmap.p)) != EELS_OK) return r1;
+        EELS_CK(cudaEventRecord(e1, st));
+        if ((r1 = contract_slice(Sin, i, 1, dscratch.p)) != EELS_OK) return r1;
+        EELS_CK(cudaEventRecord(e2, st));
+        EELS_CK(cudaEventSynchronize(e2));
+        float t_tr = 0.f, t_pr = 0.f;
+        cudaEventElapsedTime(&t_tr, e0, e1);
+        cudaEventElapsedTime(&t_pr, e1, e2);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        // the timed transition-first run accumulated this slice into the map; the
+        // remaining slices use the faster grouping
+        chosen = t_pr < t_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
+        ctx->assoc_cache[shape_key] = chosen;
+        tune = false;
+      } else {
+        eels_status r1 = contract_slice(Sin, i, pf, dmap.p);
+        if (r1 != EELS_OK) return r1;
       }
     }
     for (int b0 = slice_off[i]; !tc && b0 < slice_off[i + 1]; b0 += batch) {

@@ -79,6 +79,32 @@ __device__ __forceinline__ void put2(void* base, int64_t plane_stride, int64_t e
   }
 }
 
+// store 16 consecutive values of a row (element e, a multiple of 16) in every plane
+template <int PREC>
+__device__ __forceinline__ void put16(void* base, int64_t plane_stride, int64_t e, const float* v) {
+  if constexpr (PREC == EELS_TC_TF32) {
+    float4* d = reinterpret_cast<float4*>(static_cast<float*>(base) + e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      d[q] = make_float4(tc::to_tf32(v[4 * q]), tc::to_tf32(v[4 * q + 1]), tc::to_tf32(v[4 * q + 2]),
+                         tc::to_tf32(v[4 * q + 3]));
+  } else {
+    __align__(16) __nv_bfloat16 hi[16], lo[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      hi[q] = __float2bfloat16_rn(v[q]);
+      lo[q] = __float2bfloat16_rn(v[q] - __bfloat162float(hi[q]));
+    }
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+    uint4* dh = reinterpret_cast<uint4*>(p + e);
+    uint4* dl = reinterpret_cast<uint4*>(p + plane_stride + e);
+    dh[0] = reinterpret_cast<uint4*>(hi)[0];
+    dh[1] = reinterpret_cast<uint4*>(hi)[1];
+    dl[0] = reinterpret_cast<uint4*>(lo)[0];
+    dl[1] = reinterpret_cast<uint4*>(lo)[1];
+  }
+}
+
 struct EpiStore {
   void* out;
   int64_t z_stride;      // elements between problems
@@ -101,11 +127,27 @@ struct EpiAbs2 {
   int rows;
 };
 
+// GEMM-Y epilogue: C[r][2p + c] = Y[r][p] of one site; for every channel t write
+// BV[site*T + t][2r] = H_t[p] Y[r][p] and BV[site*T + t][2r + 1] = -i H_t[p] Y[r][p]
+// (interleaved over p), the B operand of the per-channel GEMM-V.
+struct EpiSpread {
+  void* bv;
+  int64_t z_stride;      // elements between transitions
+  int64_t plane_stride;
+  int64_t row_pitch;     // k1p
+  int rows;              // nr_cap
+  int P;                 // window pixels w*w
+  int n_types;
+  const float2* H;       // [S][T][w][w]
+  const int* slot_site;
+};
+
 template <int MODE, int PREC>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           int kblocks, const int* __restrict__ a_batch, const int* __restrict__ b_batch,
-          const int* __restrict__ n_valid, EpiStore es, EpiAbs2 ea, int* __restrict__ status) {
+          const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
+          EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
   using P = Prec<PREC>;
   using TL = Tile<PREC>;
   constexpr int STAGES = P::STAGES, BK = P::BK, PL = P::PLANES;
@@ -114,7 +156,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const int z = blockIdx.z;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int nv = n_valid[z];
-  if (n0 >= nv) return;
+  if (n0 >= nv || (m_valid && m0 >= m_valid[z])) return;
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * TL::STAGE_BYTES);
@@ -195,10 +237,33 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       float v[16];
       tc::tmem_ld16(trow + c, v);
       const int col = n0 + c;
-      if (row < es.rows && col < es.cols) {
+      if (row < es.rows && col < es.cols) put16<PREC>(es.out, es.plane_stride, rbase + col, v);
+    }
+  } else if constexpr (MODE == 2) {
+    const int site = ey.slot_site[z];
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tc::tmem_ld16(trow + c, v);
+      const int col = n0 + c;   // 2 p
+      if (row < ey.rows && col < es.cols) {
+        for (int t = 0; t < ey.n_types; ++t) {
+          const float2* Ht = ey.H + ((int64_t)site * ey.n_types + t) * ey.P;
+          const int64_t r0 = ((int64_t)z * ey.n_types + t) * ey.z_stride +
+                             (int64_t)(2 * row) * ey.row_pitch + col;
+          float hy[16], mhy[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          put2<PREC>(es.out, es.plane_stride, rbase + col + 2 * q, v[2 * q], v[2 * q + 1]);
+          for (int q = 0; q < 8; ++q) {
+            const int pp = col / 2 + q;
+            const float2 h = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
+            const float2 y = cmul(h, make_float2(v[2 * q], v[2 * q + 1]));
+            hy[2 * q] = y.x;
+            hy[2 * q + 1] = y.y;
+            mhy[2 * q] = y.y;
+            mhy[2 * q + 1] = -y.x;
+          }
+          put16<PREC>(ey.bv, ey.plane_stride, r0, hy);
+          put16<PREC>(ey.bv, ey.plane_stride, r0 + ey.row_pitch, mhy);
+        }
       }
     }
   } else {
@@ -330,6 +395,67 @@ __global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __re
   }
 }
 
+// AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
+template <int PREC>
+__global__ void k_gather_arows(const float2* __restrict__ ax, const float2* __restrict__ ay,
+                               int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
+                               const int* __restrict__ xoff, const int* __restrict__ xcnt,
+                               const int* __restrict__ xlist, const int* __restrict__ yoff,
+                               const int* __restrict__ ycnt, const int* __restrict__ ylist,
+                               int nr_cap, void* __restrict__ AY, int k2p) {
+  constexpr int PL = Prec<PREC>::PLANES;
+  const int r = blockIdx.x, slot = blockIdx.y;
+  const int s = slot_site[slot];
+  const int nx = xcnt[s], nr = nx * ycnt[s];
+  const int64_t pstride = (int64_t)nr_cap * k2p;
+  const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)r * k2p;
+  int ix = 0, iy = 0;
+  if (r < nr) {
+    ix = xlist[xoff[s] + r % nx];
+    iy = ylist[yoff[s] + r / nx];
+  }
+  for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    if (r < nr && j < n_in) a = cmul(ax[(int64_t)j * n_sx + ix], ay[(int64_t)j * n_sy + iy]);
+    put2<PREC>(AY, pstride, r0 + 2 * j, a.x, a.y);
+  }
+}
+
+// BY[slot][plane][2p][2j + c] = conj(Sin[j][p]), BY[slot][plane][2p + 1] = i conj(Sin[j][p])
+// over the window pixels p; a 32 x 32 (p, j) tile is transposed through shared memory.
+template <int PREC>
+__global__ void k_gather_sin_t(const float2* __restrict__ Sin, int nh, int n_in, int w,
+                               const int* __restrict__ slot_site, const int* __restrict__ wx,
+                               const int* __restrict__ wy, void* __restrict__ BY, int k1p,
+                               int k2p) {
+  constexpr int PL = Prec<PREC>::PLANES;
+  __shared__ float2 tile[32][33];
+  const int p0 = blockIdx.x * 32, j0 = blockIdx.y * 32, slot = blockIdx.z;
+  const int s = slot_site[slot];
+  const int P = w * w;
+  const int64_t plane = (int64_t)nh * nh;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj, p = p0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < n_in && p < P) {
+      const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
+      v = Sin[(int64_t)j * plane + (int64_t)gy * nh + gx];
+    }
+    tile[jj][tx] = v;
+  }
+  __syncthreads();
+  const int64_t pstride = (int64_t)k1p * k2p;
+  for (int pp = ty; pp < 32; pp += 8) {
+    const int p = p0 + pp, j = j0 + tx;
+    if (2 * p >= k1p || 2 * j >= k2p) continue;
+    const float2 v = tile[tx][pp];
+    const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)(2 * p) * k2p;
+    put2<PREC>(BY, pstride, r0 + 2 * j, v.x, -v.y);
+    put2<PREC>(BY, pstride, r0 + k2p + 2 * j, v.y, v.x);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -371,6 +497,8 @@ cudaError_t set_attrs() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_tc_gemm<1, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tc_gemm<2, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -405,10 +533,11 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   const int64_t pstride = (int64_t)b.n_out * b.k2p;
   EpiStore es{b.M1, Prec<PREC>::PLANES * pstride, pstride, b.k2p, b.n_out, b.k2p};
   EpiAbs2 ea{};
+  EpiSpread ey{};
   dim3 g1((b.k2p + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
   k_tc_gemm<0, PREC><<<g1, 128, Tile<PREC>::SMEM, st>>>(mA1, mB1, b.k1p / Prec<PREC>::BK,
-                                                         b.a_batch1, b.b_batch1, b.n_valid1, es,
-                                                         ea, b.status);
+                                                         b.a_batch1, b.b_batch1, b.n_valid1, nullptr,
+                                                         es, ea, ey, b.status);
   return cudaGetLastError();
 }
 
@@ -425,14 +554,90 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   EpiStore es{};
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
+  EpiSpread ey{};
   dim3 g2((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
   k_tc_gemm<1, PREC><<<g2, 128, Tile<PREC>::SMEM, st>>>(mM1, mB2, b.k2p / Prec<PREC>::BK,
-                                                         b.a_batch2, b.b_batch2, b.n_valid2, es,
-                                                         ea, b.status);
+                                                         b.a_batch2, b.b_batch2, b.n_valid2, nullptr,
+                                                         es, ea, ey, b.status);
+  return cudaGetLastError();
+}
+
+// Association with the probe sum first: gathers for GEMM-Y (A1 is shared with GEMM-V).
+template <int PREC>
+cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
+  cudaError_t e;
+  k_gather_sout<PREC><<<dim3(b.n_out, b.n_sites), 256, 0, st>>>(b.Sout, b.nh, b.n_out, b.w,
+                                                                 b.slot_site, b.wx, b.wy, b.A1,
+                                                                 b.k1p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_gather_arows<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
+      b.ax, b.ay, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt,
+      b.ylist, b.nr_cap, b.AY, b.k2p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  dim3 gt((b.k1p / 2 + 31) / 32, (b.k2p / 2 + 31) / 32, b.n_sites);
+  k_gather_sin_t<PREC><<<gt, 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.slot_site, b.wx, b.wy,
+                                            b.BY, b.k1p, b.k2p);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
+  CUtensorMap mAY, mBY;
+  if ((e = make_map<PREC>(&mAY, b.AY, b.k2p, b.nr_cap, b.slots_cap, BM)) != cudaSuccess) return e;
+  if ((e = make_map<PREC>(&mBY, b.BY, b.k2p, b.k1p, b.slots_cap, BN)) != cudaSuccess) return e;
+  const int64_t pstride = (int64_t)2 * b.nr_cap * b.k1p;
+  EpiStore es{nullptr, 0, 0, 0, 0, b.k1p};
+  EpiAbs2 ea{};
+  EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
+               b.n_types, b.H, b.slot_site};
+  dim3 g((b.k1p + BN - 1) / BN, (b.nr_cap + BM - 1) / BM, b.n_sites);
+  k_tc_gemm<2, PREC><<<g, 128, Tile<PREC>::SMEM, st>>>(mAY, mBY, b.k2p / Prec<PREC>::BK,
+                                                        b.a_batch_y, b.a_batch_y, b.n_valid_y,
+                                                        b.m_valid_y, es, ea, ey, b.status);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
+  CUtensorMap mA1, mBV;
+  if ((e = make_map<PREC>(&mA1, b.A1, b.k1p, b.n_out, b.slots_cap, BM)) != cudaSuccess) return e;
+  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, BN)) !=
+      cudaSuccess)
+    return e;
+  EpiStore es{};
+  EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
+             b.map, b.n_out};
+  EpiSpread ey{};
+  dim3 g((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
+  k_tc_gemm<1, PREC><<<g, 128, Tile<PREC>::SMEM, st>>>(mA1, mBV, b.k1p / Prec<PREC>::BK,
+                                                        b.a_batch1, b.b_batch1, b.n_valid2, nullptr,
+                                                        es, ea, ey, b.status);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t tc_gather_y(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gather_y_impl<EELS_TC_BF16X3>(b, st)
+                                  : gather_y_impl<EELS_TC_TF32>(b, st);
+}
+
+cudaError_t tc_gemm_y(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gemm_y_impl<EELS_TC_BF16X3>(b, st)
+                                  : gemm_y_impl<EELS_TC_TF32>(b, st);
+}
+
+cudaError_t tc_gemm_v(const TcBatch& b, cudaStream_t st) {
+  if (b.n_sites <= 0) return cudaSuccess;
+  return b.prec == EELS_TC_BF16X3 ? gemm_v_impl<EELS_TC_BF16X3>(b, st)
+                                  : gemm_v_impl<EELS_TC_TF32>(b, st);
+}
 
 int tc_k_align(int prec) {
   return prec == EELS_TC_BF16X3 ? Prec<EELS_TC_BF16X3>::BK : Prec<EELS_TC_TF32>::BK;

@@ -107,9 +107,16 @@ struct TcBatch {
   const int* a_batch2; const int* b_batch2; const int* n_valid2;
   double* map;
   int* status;                            // set to 1 if a bounded wait timed out
+  // association with the probe sum first (GEMM-Y then per-channel GEMM-V)
+  void* AY; void* BY; void* BV;           // a rows, S_in window transposed, H_t . Y rows
+  const int* a_batch_y; const int* n_valid_y;   // identity map and k1p per site
+  const int* m_valid_y;                         // scan positions of the site of each slot
 };
 cudaError_t tc_gather(const TcBatch& b, cudaStream_t s);   // A1, B1, B2 operand buffers
 cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t s);    // M1 = GEMM 1
 cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t s);    // map += sum_d |GEMM 2|^2
+cudaError_t tc_gather_y(const TcBatch& b, cudaStream_t s); // A1, AY, BY
+cudaError_t tc_gemm_y(const TcBatch& b, cudaStream_t s);   // BV = H_t . (a rows x Sin window)
+cudaError_t tc_gemm_v(const TcBatch& b, cudaStream_t s);   // map += sum_d |A1 x BV|^2
 
 }  // namespace eels

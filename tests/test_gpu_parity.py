@@ -24,6 +24,22 @@ EPS = {"fp32": EPS_FP32, "tf32": EPS_TC, "bf16x3": EPS_TC}
 PRECS = ("fp32", "tf32", "bf16x3")
 
 
+def variants():
+    """(precision, association) pairs: both groupings of the tensor-core contraction."""
+    out = [("fp32", "auto"), ("tf32", "auto")]
+    for prec in ("tf32", "bf16x3"):
+        out += [(prec, "transition_first"), (prec, "probe_first")]
+    return out
+
+
+def run_map(g, ctx, sm, wl, prec, assoc):
+    ctx.set_association(assoc)
+    try:
+        return g.inelastic_map_for(ctx, sm, wl, prec)
+    finally:
+        ctx.set_association("auto")
+
+
 @pytest.fixture(scope="module")
 def g():
     import torch
@@ -78,9 +94,9 @@ def test_linear_map_matches_oracle(g, ctx, n, f, seed, w):
     ref = lin.linear_map(wl) if n >= 256 else ms.quadratic_map(wl)
     sm = g.build_smatrix_for(ctx, wl)
     assert ref.max() > 0
-    for prec in PRECS:
-        got = g.inelastic_map_for(ctx, sm, wl, prec)
-        assert eps(ref, got) < EPS[prec], prec
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, wl, prec, assoc)
+        assert eps(ref, got) < EPS[prec], (prec, assoc)
 
 
 def test_rocksalt_small_full_map(g, ctx):
@@ -90,11 +106,11 @@ def test_rocksalt_small_full_map(g, ctx):
     for iy, ix in [(0, 0), (5, 2)]:
         assert np.allclose(q[:, iy, ix], ref[:, iy, ix], rtol=1e-12, atol=0)
     sm = g.build_smatrix_for(ctx, wl)
-    for prec in PRECS:
-        got = g.inelastic_map_for(ctx, sm, wl, prec)
-        assert eps(ref, got) < EPS[prec], prec
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, wl, prec, assoc)
+        assert eps(ref, got) < EPS[prec], (prec, assoc)
         for m in range(wl.n_types):
-            assert eps(ref[m], got[m]) < EPS[prec], (prec, m)
+            assert eps(ref[m], got[m]) < EPS[prec], (prec, assoc, m)
 
 
 def test_quadratic_reference_map_matches_oracle(g, ctx):
@@ -124,8 +140,8 @@ def test_quadratic_reference_subset_positions(g, ctx):
 def test_no_sites_gives_zero_map(g, ctx):
     wl = _rand(64, 1, 10).with_sites([])
     sm = g.build_smatrix_for(ctx, wl)
-    for prec in PRECS:
-        got = g.inelastic_map_for(ctx, sm, wl, prec)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, wl, prec, assoc)
         assert got.shape == (wl.n_types, wl.scan[1], wl.scan[0]) and not got.any()
 
 
@@ -134,9 +150,9 @@ def test_single_slice_and_extreme_windows(g, ctx):
         wl = _rand(64, 1, 11 + w, n_z=1, w=w, n_sites=3)
         ref = ms.quadratic_map(wl)
         sm = g.build_smatrix_for(ctx, wl)
-        for prec in PRECS:
-            got = g.inelastic_map_for(ctx, sm, wl, prec)
-            assert eps(ref, got) < EPS[prec], (w, prec)
+        for prec, assoc in variants():
+            got = run_map(g, ctx, sm, wl, prec, assoc)
+            assert eps(ref, got) < EPS[prec], (w, prec, assoc)
 
 
 def test_site_outside_every_window_contributes_nothing(g, ctx):
@@ -200,10 +216,10 @@ def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
     ref = ms.quadratic_map(sub, positions=pos)
     r = np.array([ref[:, iy, ix] for iy, ix in pos])
     assert r.max() > 0
-    for prec in PRECS:
-        got = g.inelastic_map_for(ctx, sm, sub, prec)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, sub, prec, assoc)
         t = np.array([got[:, iy, ix] for iy, ix in pos])
-        assert eps(r, t) < EPS[prec], prec
+        assert eps(r, t) < EPS[prec], (prec, assoc)
 
 
 @pytest.mark.parametrize("name,targets,probes", [
@@ -229,7 +245,7 @@ def test_large_workloads_sampled(g, ctx, name, targets, probes):
     ref = ms.quadratic_map(sub, positions=probes)
     r = np.array([ref[:, iy, ix] for iy, ix in probes])
     assert r.max() > 0
-    for prec in PRECS:
-        got = g.inelastic_map_for(ctx, sm, sub, prec)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, sub, prec, assoc)
         t = np.array([got[:, iy, ix] for iy, ix in probes])
-        assert eps(r, t) < EPS[prec], (prec, eps(r, t))
+        assert eps(r, t) < EPS[prec], (prec, assoc, eps(r, t))
