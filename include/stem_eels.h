@@ -95,6 +95,8 @@ typedef struct {
   const double* x;        /* [n_sites] Angstrom */
   const double* y;        /* [n_sites] Angstrom */
   int on_device;          /* 1: H is a device pointer (the small per-site arrays are always host) */
+  int h_shared;           /* 1: H is [n_types][w][w], the same transition potentials at every
+                             site (windows still placed per site); 0: per-site H as above */
 } eels_transitions;
 
 /* Scan raster: R(ix, iy) = (x0 + ix*step_x, y0 + iy*step_y), Angstrom. */
@@ -119,6 +121,8 @@ const char* eels_last_error(const eels_ctx* ctx);
  * device cannot hold n_z * n_in * (N/2)^2 * 8 bytes plus the transmissions. */
 eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* optics,
                                void* stream, eels_smatrix** out);
+/* Releases the handle in stream order on the stream it was built on, which must
+ * still exist; the call waits for that stream's queued work first. */
 void eels_smatrix_free(eels_smatrix* sm);
 
 /* Shape of a built S-matrix: grid, slices and number of probe beams. */
@@ -206,6 +210,55 @@ int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
 eels_status eels_build_smatrix_static(const eels_specimen* spec, const eels_optics* optics,
                                       float* s_in, int64_t s_in_bytes, int* n_in_out,
                                       void* stream, char* err, int err_cap);
+
+/* ---------------------------------------------------------------------------
+ * Map server (not in the paper: a serving loop around the calls above).
+ * A request is one complete map: S-matrix build plus inelastic map.  Requests are
+ * queued in arrival order and admitted when one of `slots` workers is free and the
+ * request's device footprint (eels_request_footprint) fits in what is left of
+ * hbm_budget bytes; admission is first-fit in arrival order, and a request bypassed
+ * eight times stops further bypassing until it is admitted.  Each worker has its own
+ * context and non-blocking stream, so admitted requests overlap on the device; a
+ * request's S_in stays resident until its map is done.
+ * --------------------------------------------------------------------------- */
+typedef struct eels_server eels_server;
+
+typedef struct {
+  eels_specimen spec;        /* host vproj */
+  eels_optics optics;
+  eels_transitions tr;       /* host arrays */
+  eels_scan scan;
+  double beta;
+  int precision;             /* eels_precision */
+} eels_request;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> done latency of completed requests */
+  double mean_wait_ms;                      /* submit -> admission */
+  double makespan_s;                        /* first submit -> last completion */
+  double pixel_slices_per_s;                /* sum of n_scan n_z of completed requests / makespan */
+  int64_t peak_bytes;                       /* largest sum of admitted footprints */
+} eels_server_stats;
+
+/* Device bytes the server reserves for a request while it runs: transmissions, S_in,
+ * the larger of the forward and backward work arrays, a 4 GiB cap for contraction
+ * buffers and the transition potentials.  -1 for invalid sizes. */
+int64_t eels_request_footprint(const eels_request* req);
+/* Start `slots` workers on `device` sharing an HBM budget of hbm_budget bytes. */
+eels_status eels_server_create(int device, int64_t hbm_budget, int slots, eels_server** out);
+/* Queue a request; its input arrays are BORROWED until eels_server_wait has returned
+ * for it.  *id identifies it.  EELS_ERR_OOM if its footprint exceeds the whole budget,
+ * EELS_ERR_ARG for device inputs or invalid sizes. */
+eels_status eels_server_submit(eels_server* sv, const eels_request* req, int64_t* id);
+/* Block until request id is done (timeout_s <= 0: no limit) and copy its FP64 map
+ * [n_types][n_sy][n_sx] to host map_out (may be NULL); *latency_s (if non-NULL) gets its
+ * submit-to-completion time.  Returns the request's own status, or EELS_ERR_TIMEOUT. */
+eels_status eels_server_wait(eels_server* sv, int64_t id, double* map_out, double timeout_s,
+                             double* latency_s);
+eels_status eels_server_stats_get(eels_server* sv, eels_server_stats* out);
+/* Stop the workers after their current requests; requests not yet admitted are dropped. */
+void eels_server_destroy(eels_server* sv);
 
 /* Number of f-lattice beams with lambda |k| <= angle (Sec. III, pi alpha^2 L^2 / f^2). */
 int eels_count_beams(int n, double cell, double lambda, int f, double angle);

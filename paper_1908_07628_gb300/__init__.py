@@ -7,4 +7,5 @@ it and marshals arguments to it.
 from ._lib import (Context, EelsError, SMatrix, build_smatrix_for, build_smatrix_static,  # noqa: F401
                    count_beams,
                    footprint_bytes, inelastic_map_for, load, memory_model,
-                   quadratic_reference_map_for, EXPORTS, LIB_PATH)
+                   quadratic_reference_map_for, EXPORTS, LIB_PATH, Server, make_request,
+                   request_footprint)

@@ -40,12 +40,24 @@ class Transitions(C.Structure):
     _fields_ = [("n_sites", C.c_int), ("n_types", C.c_int), ("w", C.c_int),
                 ("H", C.c_void_p), ("slice", C.c_void_p), ("win_x0", C.c_void_p),
                 ("win_y0", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p),
-                ("on_device", C.c_int)]
+                ("on_device", C.c_int), ("h_shared", C.c_int)]
 
 
 class Scan(C.Structure):
     _fields_ = [("n_sx", C.c_int), ("n_sy", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
                 ("step_x", C.c_double), ("step_y", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("spec", Specimen), ("optics", Optics), ("tr", Transitions), ("scan", Scan),
+                ("beta", C.c_double), ("precision", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_ms", C.c_double), ("mean_wait_ms", C.c_double), ("makespan_s", C.c_double),
+                ("pixel_slices_per_s", C.c_double), ("peak_bytes", C.c_int64)]
 
 
 EXPORTS = {
@@ -72,6 +84,13 @@ EXPORTS = {
     "eels_build_smatrix_static": (C.c_int, [C.POINTER(Specimen), C.POINTER(Optics), C.c_void_p,
                                             C.c_int64, C.POINTER(C.c_int), C.c_void_p,
                                             C.c_char_p, C.c_int]),
+    "eels_request_footprint": (C.c_int64, [C.POINTER(Request)]),
+    "eels_server_create": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_void_p)]),
+    "eels_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "eels_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_double,
+                                   C.POINTER(C.c_double)]),
+    "eels_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "eels_server_destroy": (None, [C.c_void_p]),
     "eels_count_beams": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double]),
     "eels_memory_model": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     "eels_footprint_bytes": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -196,7 +215,7 @@ class Context:
         """eels_inelastic_map: FP64 map [n_types][n_sy][n_sx] (numpy, or into a CUDA tensor)."""
         tr, keep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
         sc = Scan(*[int(v) for v in scan[:2]], *[float(v) for v in scan[2:]])
-        shape = (int(H.shape[1]), int(scan[1]), int(scan[0]))
+        shape = (int(H.shape[-3]), int(scan[1]), int(scan[0]))
         out_arr = np.zeros(shape) if out is None else out
         o, o_dev, okeep = _ptr(out_arr, np.float64)
         st = self._lib.eels_inelastic_map(self._h, sm._h, C.byref(tr), C.byref(sc), float(beta),
@@ -219,7 +238,7 @@ class Context:
         op = Optics(float(lam), float(sigma), float(dz), int(f), float(alpha))
         tr, keep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
         sc = Scan(*[int(x) for x in scan[:2]], *[float(x) for x in scan[2:]])
-        out = np.zeros((int(H.shape[1]), int(scan[1]), int(scan[0])))
+        out = np.zeros((int(H.shape[-3]), int(scan[1]), int(scan[0])))
         steps = C.c_int64(0)
         if positions is None:
             pp, npos, pkeep = None, 0, None
@@ -273,6 +292,7 @@ class SMatrix:
 
 
 def _transitions(H, site_slice, win_x0, win_y0, site_x, site_y):
+    """H is [S][T][w][w] (per site) or [T][w][w] (the same potentials at every site)."""
     h, h_dev, hk = _ptr(H, np.complex64)
     arrs = [np.ascontiguousarray(site_slice, dtype=np.int32),
             np.ascontiguousarray(win_x0, dtype=np.int32),
@@ -280,7 +300,10 @@ def _transitions(H, site_slice, win_x0, win_y0, site_x, site_y):
             np.ascontiguousarray(site_x, dtype=np.float64),
             np.ascontiguousarray(site_y, dtype=np.float64)]
     ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
-    tr = Transitions(int(H.shape[0]), int(H.shape[1]), int(H.shape[2]), h, *ptrs, h_dev)
+    shared = len(H.shape) == 3
+    n_sites = int(arrs[0].shape[0])
+    tshape = H.shape if shared else H.shape[1:]
+    tr = Transitions(n_sites, int(tshape[0]), int(tshape[1]), h, *ptrs, h_dev, 1 if shared else 0)
     return tr, (hk, arrs)
 
 
@@ -340,3 +363,75 @@ def quadratic_reference_map_for(ctx: Context, wl, positions=None, stream=None):
                                        wl.H, wl.site_slice, wl.win_x0, wl.win_y0, wl.site_x,
                                        wl.site_y, wl.scan, wl.beta, positions=positions,
                                        stream=stream)
+
+
+# -- map server --------------------------------------------------------------------------
+
+def make_request(vproj, cell, lam, sigma, dz, f, alpha, H, site_slice, win_x0, win_y0, site_x,
+                 site_y, scan, beta, precision="tf32"):
+    """eels_request over host arrays; returns (request, keepalive)."""
+    v, on_dev, vkeep = _ptr(vproj, np.float32)
+    if on_dev:
+        raise TypeError("server requests take host arrays")
+    n_z, n = int(vproj.shape[0]), int(vproj.shape[-1])
+    tr, tkeep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
+    req = Request(Specimen(n, n_z, float(cell), v, 0),
+                  Optics(float(lam), float(sigma), float(dz), int(f), float(alpha)), tr,
+                  Scan(*[int(x) for x in scan[:2]], *[float(x) for x in scan[2:]]), float(beta),
+                  EELS_PREC[precision])
+    return req, (vkeep, tkeep)
+
+
+def request_footprint(req) -> int:
+    return int(load().eels_request_footprint(C.byref(req)))
+
+
+class Server:
+    """eels_server: continuous-batching map server on one device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 64 << 30, slots: int = 4):
+        self._lib = load()
+        h = C.c_void_p()
+        st = self._lib.eels_server_create(int(device), int(hbm_budget), int(slots), C.byref(h))
+        if st != 0:
+            raise EelsError(st, "eels_server_create")
+        self._h = h
+        self._keep = {}
+        self._shape = {}
+
+    def submit(self, req, keep, n_types, scan) -> int:
+        rid = C.c_int64(0)
+        st = self._lib.eels_server_submit(self._h, C.byref(req), C.byref(rid))
+        if st != 0:
+            raise EelsError(st, "eels_server_submit")
+        self._keep[rid.value] = (req, keep)
+        self._shape[rid.value] = (int(n_types), int(scan[1]), int(scan[0]))
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 0.0):
+        out = np.zeros(self._shape[rid])
+        lat = C.c_double(0.0)
+        st = self._lib.eels_server_wait(self._h, int(rid), out.ctypes.data_as(C.c_void_p),
+                                        float(timeout), C.byref(lat))
+        if st == 5:
+            raise EelsError(st, "eels_server_wait timed out")
+        self._keep.pop(rid, None)
+        if st != 0:
+            raise EelsError(st, f"request {rid} failed")
+        return out, float(lat.value)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._lib.eels_server_stats_get(self._h, C.byref(s))
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.eels_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

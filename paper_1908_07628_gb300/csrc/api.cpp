@@ -40,6 +40,7 @@ struct eels_smatrix {
   float2* t = nullptr;         // [n_z][n][n]
   float2* ptab = nullptr;      // [n/2][n/2] box order, forward propagator / N^2
   float2* s_in = nullptr;      // [n_z][n_in][n/2][n/2]
+  cudaStream_t st = nullptr;   // stream the handle's memory is ordered on
 };
 
 namespace {
@@ -322,9 +323,13 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
   auto bail = [&](eels_status code) { eels_smatrix_free(sm); return code; };
   const int64_t plane = (int64_t)nh * nh;
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&sm->t, sizeof(float2) * (size_t)n_z * n * n)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&sm->ptab, sizeof(float2) * (size_t)plane)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&sm->s_in, sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane))) !=
+  sm->st = st;
+  // stream-ordered: no device-wide synchronisation against other streams' work
+  if ((e = cudaMallocAsync((void**)&sm->t, sizeof(float2) * (size_t)n_z * n * n, st)) !=
+          cudaSuccess ||
+      (e = cudaMallocAsync((void**)&sm->ptab, sizeof(float2) * (size_t)plane, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void**)&sm->s_in,
+                           sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane), st)) !=
           cudaSuccess)
     return bail(cuda_fail(ctx, e, "S-matrix allocation"));
   if ((r = build_slices(ctx, spec, op, st, sm->t, sm->ptab)) != EELS_OK) return bail(r);
@@ -367,9 +372,10 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
 void eels_smatrix_free(eels_smatrix* sm) {
   if (!sm) return;
   cudaSetDevice(sm->ctx->device);
-  cudaFree(sm->t);
-  cudaFree(sm->ptab);
-  cudaFree(sm->s_in);
+  cudaStreamSynchronize(sm->st);
+  if (sm->t) cudaFreeAsync(sm->t, sm->st);
+  if (sm->ptab) cudaFreeAsync(sm->ptab, sm->st);
+  if (sm->s_in) cudaFreeAsync(sm->s_in, sm->st);
   delete sm;
 }
 
@@ -427,6 +433,7 @@ eels_status check_transitions(eels_ctx* ctx, const eels_transitions* tr, const e
   if (!tr || !sc) return fail(ctx, EELS_ERR_ARG, "null transitions/scan");
   if (tr->n_sites < 0 || tr->n_types <= 0 || tr->w < 1 || tr->w > n / 2)
     return fail(ctx, EELS_ERR_ARG, "bad transition sizes (need 1 <= w <= N/2)");
+  if (tr->h_shared != 0 && tr->h_shared != 1) return fail(ctx, EELS_ERR_ARG, "bad h_shared");
   if (tr->n_sites > 0 &&
       (!tr->H || !tr->slice || !tr->win_x0 || !tr->win_y0 || !tr->x || !tr->y))
     return fail(ctx, EELS_ERR_ARG, "null transition array");
@@ -485,7 +492,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   DevBuf<int> dwx, dwy, dxoff, dxcnt, dxlist, dyoff, dycnt, dylist, dpx, dpy, dbp, dbq, dts, dtt;
   DevBuf<double> dmap;
   const float2* H = (const float2*)tr->H;
-  const size_t hcount = (size_t)S * T * w * w;
+  const int h_mul = tr->h_shared ? 0 : 1;
+  const size_t hcount = (size_t)(tr->h_shared ? 1 : S) * T * w * w;
   if (!tr->on_device) {
     EELS_CK(dH.upload((const float2*)tr->H, hcount, st));
     H = dH.p;
@@ -636,7 +644,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       eels::TcBatch b{};
       b.prec = tc_prec;
       b.Sout = Sout.p; b.Sin = Sin; b.nh = nh; b.n_out = n_out; b.n_in = n_in; b.w = w;
-      b.n_types = T; b.H = H; b.wx = dwx.p; b.wy = dwy.p;
+      b.n_types = T; b.H = H; b.h_mul = h_mul; b.wx = dwx.p; b.wy = dwy.p;
       b.slot_site = dslot.p + q0; b.z_site = dzs.p + (int64_t)q0 * T;
       b.z_type = dzt.p + (int64_t)q0 * T; b.n_sites = ns; b.slots_cap = sb;
       b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
@@ -725,8 +733,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       eels::TransitionBatch tb{dts.p + b0, dtt.p + b0, std::min(batch, slice_off[i + 1] - b0)};
       {
         Prof pr(ctx, "gemm1_fp32", st);
-        EELS_CK(eels::launch_gemm1_fp32(Sout.p, Sin, nh, n_out, n_in, w, H, T, tb, dwx.p, dwy.p,
-                                        M.p, m_stride, st));
+        EELS_CK(eels::launch_gemm1_fp32(Sout.p, Sin, nh, n_out, n_in, w, H, T, h_mul, tb, dwx.p,
+                                        dwy.p, M.p, m_stride, st));
       }
       {
         Prof pr(ctx, "gemm2_abs2_fp32", st);
@@ -808,7 +816,7 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
   if ((r = build_slices(ctx, spec, op, st, t.p, ptab.p)) != EELS_OK) return r;
   const float2* H = (const float2*)tr->H;
   if (!tr->on_device) {
-    EELS_CK(dH.upload((const float2*)tr->H, (size_t)S * T * w * w, st));
+    EELS_CK(dH.upload((const float2*)tr->H, (size_t)(tr->h_shared ? 1 : S) * T * w * w, st));
     H = dH.p;
   }
   DevBuf<int> dwx, dwy, dbp, dbq;
@@ -905,7 +913,8 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
                          sp_off[i + 1] - sp_off[i], active};
       {
         Prof pr(ctx, "spawn", st);
-        EELS_CK(eels::launch_spawn(n, sl, D.p, H, T, w, dwx.p, dwy.p, Phi.p, tw, st));
+        EELS_CK(eels::launch_spawn(n, sl, D.p, H, T, tr->h_shared ? 0 : 1, w, dwx.p, dwy.p, Phi.p,
+                                   tw, st));
       }
       active += sl.count;
       const bool last = (i == n_z - 1);

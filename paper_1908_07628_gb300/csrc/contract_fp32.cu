@@ -29,7 +29,8 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 
 __global__ void __launch_bounds__(256)
 k_gemm1(const float2* __restrict__ Sout, const float2* __restrict__ Sin, int nh, int n_out,
-        int n_in, int w, const float2* __restrict__ H, int n_types, const int* __restrict__ tr_site,
+        int n_in, int w, const float2* __restrict__ H, int n_types, int h_mul,
+        const int* __restrict__ tr_site,
         const int* __restrict__ tr_type, const int* __restrict__ win_x0,
         const int* __restrict__ win_y0, float2* __restrict__ M, int64_t m_stride) {
   __shared__ float2 As[TK][TM + 1];
@@ -38,7 +39,7 @@ k_gemm1(const float2* __restrict__ Sout, const float2* __restrict__ Sin, int nh,
   __shared__ float2 hk[TK];
   const int t = blockIdx.z;
   const int s = tr_site[t];
-  const float2* Ht = H + ((int64_t)s * n_types + tr_type[t]) * w * w;
+  const float2* Ht = H + ((int64_t)s * h_mul * n_types + tr_type[t]) * w * w;
   const int x0 = win_x0[s], y0 = win_y0[s];
   const int d0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -219,13 +220,13 @@ __global__ void k_scale(double* a, int64_t count, double scale) {
 }  // namespace
 
 cudaError_t launch_gemm1_fp32(const float2* Sout, const float2* Sin, int nh, int n_out, int n_in,
-                              int w, const float2* H, int n_types, const TransitionBatch& tb,
-                              const int* win_x0, const int* win_y0, float2* M, int64_t m_stride,
-                              cudaStream_t s) {
+                              int w, const float2* H, int n_types, int h_mul,
+                              const TransitionBatch& tb, const int* win_x0, const int* win_y0,
+                              float2* M, int64_t m_stride, cudaStream_t s) {
   if (tb.count <= 0) return cudaSuccess;
   dim3 grid((n_in + TN - 1) / TN, (n_out + TM - 1) / TM, tb.count);
-  k_gemm1<<<grid, 256, 0, s>>>(Sout, Sin, nh, n_out, n_in, w, H, n_types, tb.site, tb.type, win_x0,
-                               win_y0, M, m_stride);
+  k_gemm1<<<grid, 256, 0, s>>>(Sout, Sin, nh, n_out, n_in, w, H, n_types, h_mul, tb.site, tb.type,
+                               win_x0, win_y0, M, m_stride);
   return cudaGetLastError();
 }
 

@@ -138,7 +138,8 @@ struct EpiSpread {
   int rows;              // nr_cap
   int P;                 // window pixels w*w
   int n_types;
-  const float2* H;       // [S][T][w][w]
+  const float2* H;       // [S][T][w][w], or [T][w][w] shared by all sites (h_mul = 0)
+  int h_mul;
   const int* slot_site;
 };
 
@@ -247,7 +248,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       const int col = n0 + c;   // 2 p
       if (row < ey.rows && col < es.cols) {
         for (int t = 0; t < ey.n_types; ++t) {
-          const float2* Ht = ey.H + ((int64_t)site * ey.n_types + t) * ey.P;
+          const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t) * ey.P;
           const int64_t r0 = ((int64_t)z * ey.n_types + t) * ey.z_stride +
                              (int64_t)(2 * row) * ey.row_pitch + col;
           float hy[16], mhy[16];
@@ -342,7 +343,7 @@ __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out
 template <int PREC>
 __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in, int w,
                                const int* __restrict__ z_site, const int* __restrict__ z_type,
-                               const float2* __restrict__ H, int n_types,
+                               const float2* __restrict__ H, int n_types, int h_mul,
                                const int* __restrict__ wx, const int* __restrict__ wy,
                                void* __restrict__ B1, int k1p) {
   constexpr int PL = Prec<PREC>::PLANES;
@@ -352,7 +353,7 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
   const int64_t pstride = (int64_t)2 * n_in * k1p;
   const int64_t r0 = (int64_t)z * PL * pstride + (int64_t)(2 * j) * k1p;
   const int64_t r1 = r0 + k1p;
-  const float2* Hz = H + ((int64_t)s * n_types + z_type[z]) * w * w;
+  const float2* Hz = H + ((int64_t)s * h_mul * n_types + z_type[z]) * w * w;
   const float2* src = Sin + (int64_t)j * plane;
   const int P = w * w;
   for (int p = threadIdx.x; p < k1p / 2; p += blockDim.x) {
@@ -512,8 +513,8 @@ cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
                                                                  b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_sin_h<PREC><<<dim3(b.n_in, nz), 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.z_site,
-                                                          b.z_type, b.H, b.n_types, b.wx, b.wy,
-                                                          b.B1, b.k1p);
+                                                          b.z_type, b.H, b.n_types, b.h_mul, b.wx,
+                                                          b.wy, b.B1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_probe<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
       b.ax, b.ay, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt,
@@ -591,7 +592,7 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiStore es{nullptr, 0, 0, 0, 0, b.k1p};
   EpiAbs2 ea{};
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
-               b.n_types, b.H, b.slot_site};
+               b.n_types, b.H, b.h_mul, b.slot_site};
   dim3 g((b.k1p + BN - 1) / BN, (b.nr_cap + BM - 1) / BM, b.n_sites);
   k_tc_gemm<2, PREC><<<g, 128, Tile<PREC>::SMEM, st>>>(mAY, mBY, b.k2p / Prec<PREC>::BK,
                                                         b.a_batch_y, b.a_batch_y, b.n_valid_y,

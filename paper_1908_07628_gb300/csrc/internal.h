@@ -53,9 +53,10 @@ struct SpawnList {
   int count;
   int first_wave;     // output wave index of the first spawn
 };
+// H is [S][T][w][w], or [T][w][w] shared by every site when h_mul = 0.
 cudaError_t launch_spawn(int n, const SpawnList& sp, const float2* D, const float2* H, int n_types,
-                         int w, const int* win_x0, const int* win_y0, float2* Phi, const float2* tw,
-                         cudaStream_t s);
+                         int h_mul, int w, const int* win_x0, const int* win_y0, float2* Phi,
+                         const float2* tw, cudaStream_t s);
 
 // Contraction (CUDA cores, FP32).
 struct TransitionBatch {
@@ -69,9 +70,9 @@ struct WindowLists {
   int max_nr;                                           // max over sites of xcnt*ycnt
 };
 cudaError_t launch_gemm1_fp32(const float2* Sout, const float2* Sin, int nh, int n_out, int n_in,
-                              int w, const float2* H, int n_types, const TransitionBatch& tb,
-                              const int* win_x0, const int* win_y0, float2* M, int64_t m_stride,
-                              cudaStream_t s);
+                              int w, const float2* H, int n_types, int h_mul,
+                              const TransitionBatch& tb, const int* win_x0, const int* win_y0,
+                              float2* M, int64_t m_stride, cudaStream_t s);
 cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out, int n_in,
                                    const float2* ax, const float2* ay, int n_sx, int n_sy,
                                    const TransitionBatch& tb, const WindowLists& wl, double* map,
@@ -92,7 +93,8 @@ struct TcBatch {
   int prec;                               // EELS_TC_TF32 or EELS_TC_BF16X3
   const float2* Sout; const float2* Sin;  // depth planes [beam][nh][nh]
   int nh, n_out, n_in, w, n_types;
-  const float2* H;                        // [S][T][w][w]
+  const float2* H;                        // [S][T][w][w] or shared [T][w][w]
+  int h_mul;                              // 1: per-site H, 0: shared
   const int* wx; const int* wy;           // per site window origin
   const int* slot_site;                   // [n_sites] site of each slot of this batch
   const int* z_site; const int* z_type;   // [n_sites * T] transition z = slot*T + type

@@ -343,7 +343,7 @@ __global__ void k_probe_init(float2* __restrict__ W, int n, const double* __rest
 // equals the spectrum of the Fourier-interpolated wave.
 __global__ void k_spawn(int n, const int* __restrict__ src, const int* __restrict__ site,
                         const int* __restrict__ type, int first_wave, const float2* __restrict__ D,
-                        const float2* __restrict__ H, int n_types, int w,
+                        const float2* __restrict__ H, int n_types, int h_mul, int w,
                         const int* __restrict__ win_x0, const int* __restrict__ win_y0,
                         float2* __restrict__ Phi, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
@@ -366,7 +366,7 @@ __global__ void k_spawn(int n, const int* __restrict__ src, const int* __restric
     return;
   }
   const float2* drow = D + (int64_t)src[k] * nh * nh + (int64_t)(y / 2) * nh;
-  const float2* hrow = H + (((int64_t)s * n_types + type[k]) * w + v) * w;
+  const float2* hrow = H + (((int64_t)s * h_mul * n_types + type[k]) * w + v) * w;
   for (int u = threadIdx.x; u < w; u += blockDim.x) {
     const int g = (win_x0[s] + u) % nh;
     gcol[u] = g;
@@ -482,13 +482,13 @@ cudaError_t launch_probe_init(float2* W, int n, int n_probes, const double* rx, 
 }
 
 cudaError_t launch_spawn(int n, const SpawnList& sp, const float2* D, const float2* H, int n_types,
-                         int w, const int* win_x0, const int* win_y0, float2* Phi,
+                         int h_mul, int w, const int* win_x0, const int* win_y0, float2* Phi,
                          const float2* tw, cudaStream_t s) {
   if (sp.count <= 0) return cudaSuccess;
   dim3 grid(n, sp.count);
   const size_t smem = (size_t)w * (sizeof(float2) + sizeof(int));
-  k_spawn<<<grid, 256, smem, s>>>(n, sp.src, sp.site, sp.type, sp.first_wave, D, H, n_types, w,
-                                  win_x0, win_y0, Phi, tw);
+  k_spawn<<<grid, 256, smem, s>>>(n, sp.src, sp.site, sp.type, sp.first_wave, D, H, n_types,
+                                  h_mul, w, win_x0, win_y0, Phi, tw);
   return cudaGetLastError();
 }
 

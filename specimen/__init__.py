@@ -348,3 +348,88 @@ WORKLOADS = {
     "rocksalt_vacancy": rocksalt_vacancy,
     "nanoparticle": nanoparticle,
 }
+
+
+# ----------------------------------------------------------------------------
+# mixed request stream for the map server
+# ----------------------------------------------------------------------------
+
+_M_ORDER = (0, 1, -1, 2, -2, 3)
+_MASTERS = {}
+
+
+def _master_crystal(n: int, max_slices: int = 120):
+    """Rocksalt crystal of N/64 cells per side (0.0672 A pixels), max_slices thick.
+
+    The crystal repeats every two slices (dz = a/2), so only two slices of potential
+    are evaluated and then tiled.  Returns (vproj [max_slices][n][n], Fe sites x, y,
+    slice) shared by every request on this grid.
+    """
+    if n in _MASTERS:
+        return _MASTERS[n]
+    ncell = n // 64
+    a = A_FEO
+    L = ncell * a
+    x, y, z, sp, lay = rocksalt_atoms(a, ncell, ncell, 1)
+    two = projected_potentials(n, L, 2, x, y, sp, lay)
+    vproj = np.ascontiguousarray(np.tile(two, (max_slices // 2, 1, 1)))
+    fe = sp == "Fe"
+    fx, fy, fl = x[fe], y[fe], lay[fe]
+    reps = max_slices // 2
+    sx = np.tile(fx, reps)
+    sy = np.tile(fy, reps)
+    ss = (np.repeat(np.arange(reps), fx.size) * 2 + np.tile(fl, reps)).astype(np.int32)
+    _MASTERS[n] = (vproj, sx, sy, ss, L)
+    return _MASTERS[n]
+
+
+def serving_request(rng, w: int = 32):
+    """One map request of the mixed stream: grid 256^2..1024^2, 20..120 slices, 1..6
+    transition channels, f in {2, 3, 4}, scan 16^2..64^2 over the central unit cell.
+
+    Returns a dict of host arrays; vproj is a view of the first n_z slices of the
+    grid's master crystal and H is one [T][w][w] set shared by all Fe sites (every
+    site sits on a pixel of the N/2 grid, so the same samples apply to all of them).
+    """
+    n = int(rng.choice([256, 384, 512, 768, 1024]))
+    n_z = int(rng.integers(10, 61)) * 2
+    T = int(rng.integers(1, 7))
+    f = int(rng.choice([2, 3, 4]))
+    ns = int(rng.integers(16, 65))
+    vproj, sx, sy, ss, L = _master_crystal(n)
+    keep = ss < n_z
+    nh = n // 2
+    px = L / nh
+    sxk, syk, ssk = sx[keep], sy[keep], ss[keep]
+    wx = ((np.floor(sxk / px + 0.5).astype(np.int64) - w // 2) % nh).astype(np.int32)
+    wy = ((np.floor(syk / px + 0.5).astype(np.int64) - w // 2) % nh).astype(np.int32)
+    # shared H sampled about a site on a pixel: window origin at -w/2
+    u = (np.arange(w) - w // 2) * px
+    DX, DY = np.meshgrid(u, u)
+    r = np.hypot(DX, DY)
+    phi = np.arctan2(DY, DX)
+    H = np.stack([0.01 * (r / 0.3) ** abs(m) * np.exp(-r * r / 0.18) * np.exp(1j * m * phi)
+                  for m in _M_ORDER[:T]]).astype(np.complex64)
+    c0 = (L // A_FEO // 2) * A_FEO
+    return {"n": n, "n_z": n_z, "cell": L, "f": f, "n_types": T, "vproj": vproj[:n_z],
+            "H": H, "site_slice": ssk.copy(), "site_x": sxk.copy(), "site_y": syk.copy(),
+            "win_x0": wx, "win_y0": wy, "scan": (ns, ns, c0, c0, A_FEO / ns, A_FEO / ns),
+            "lam": LAM_200KEV, "sigma": interaction_constant(200e3, LAM_200KEV),
+            "dz": A_FEO / 2, "alpha": 0.020, "beta": 0.030}
+
+
+def serving_stream(count: int, seed: int = 4, accept=None):
+    """`count` requests with unit-mean exponential inter-arrival gaps (seeded).
+
+    accept(request) -> bool may reject a draw (for example one whose device footprint
+    exceeds the server budget); rejected draws are replaced by the next ones.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        req = serving_request(rng)
+        gap = float(rng.exponential(1.0))
+        if accept is None or accept(req):
+            req["gap"] = gap
+            out.append(req)
+    return out

@@ -249,3 +249,24 @@ def test_large_workloads_sampled(g, ctx, name, targets, probes):
         got = run_map(g, ctx, sm, sub, prec, assoc)
         t = np.array([got[:, iy, ix] for iy, ix in probes])
         assert eps(r, t) < EPS[prec], (prec, assoc, eps(r, t))
+
+
+def test_shared_transition_potentials_equal_per_site_copies(g, ctx):
+    """h_shared: one [T][w][w] H for every site gives the map of the per-site copies."""
+    wl = _rand(128, 2, 15, n_sites=6, w=12)
+    Hs = np.ascontiguousarray(wl.H[0])
+    wl_rep = wl.with_sites(np.arange(wl.n_sites))
+    wl_rep.H = np.ascontiguousarray(np.broadcast_to(Hs, wl.H.shape))
+    sm = g.build_smatrix_for(ctx, wl)
+    for prec, assoc in variants():
+        a = run_map(g, ctx, sm, wl_rep, prec, assoc)
+        ctx.set_association(assoc)
+        b = ctx.inelastic_map(sm, Hs, wl.site_slice, wl.win_x0, wl.win_y0, wl.site_x, wl.site_y,
+                              wl.scan, wl.beta, precision=prec)
+        ctx.set_association("auto")
+        assert a.max() > 0 and np.allclose(a, b, rtol=1e-12, atol=0), (prec, assoc)
+    qa, _ = g.quadratic_reference_map_for(ctx, wl_rep)
+    qb, _ = ctx.quadratic_reference_map(wl.vproj, wl.cell, wl.lam, wl.sigma, wl.dz, wl.f,
+                                        wl.alpha, Hs, wl.site_slice, wl.win_x0, wl.win_y0,
+                                        wl.site_x, wl.site_y, wl.scan, wl.beta)
+    assert np.allclose(qa, qb, rtol=1e-12, atol=0)
