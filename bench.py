@@ -222,6 +222,7 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     wl = load_workload(args)
     ctx = g.Context(dev)
+    ctx.set_association(args.association)
     stream = torch.cuda.current_stream()
     vdev = torch.from_numpy(wl.vproj).cuda()
     Hdev = torch.from_numpy(wl.H).cuda()
@@ -374,7 +375,8 @@ def gpu_arm(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": {"tf32": "tf32", "bf16x3": "bf16x3"}.get(args.precision, "f32"), "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "n_in": n_in,
                    "n_out": n_out, "scan": [wl.scan[0], wl.scan[1]], "n_types": wl.n_types,
-                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "precision": args.precision, "association": args.association,
+                   "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (S_in alone is "
                          f"{wl.n_z * n_in * (wl.n // 2) ** 2 * 8 / 1e9:.1f} GB)"},
         "e2e": {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -534,6 +536,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sp.WORKLOADS))
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--quad-probes", type=int, default=8)
+    ap.add_argument("--association", default="auto",
+                    choices=["auto", "transition_first", "probe_first"])
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")

@@ -342,11 +342,33 @@ def random_workload(n: int, n_z: int, f: int, cell: float, n_sites: int, w: int,
                     site_slice=ss, site_x=sx, site_y=sy, win_x0=wx, win_y0=wy, scan=scan)
 
 
+def nanoparticle_small():
+    """Fe-O sphere (30 A) in a 40 A box, dz = 2 A, 20 slices, 512^2 grid, f = 4,
+    48x48 scan at 0.625 A: a few-GB case of the nanoparticle workload for profiling."""
+    a, box, n, f, w = A_FEO, 40.0, 512, 4, 24
+    dz = 2.0
+    n_z = 20
+    x, y, z, sp = nanoparticle_atoms(a, 30.0, box)
+    lay = np.floor(z / dz + 1e-9).astype(np.int32)
+    keep = lay < n_z
+    x, y, z, sp, lay = x[keep], y[keep], z[keep], sp[keep], lay[keep]
+    vproj = projected_potentials(n, box, n_z, x, y, sp, lay)
+    fe = sp == "Fe"
+    H, wx, wy = transition_windows(n, box, w, x[fe], y[fe])
+    scan = (48, 48, 5.0, 5.0, 0.625, 0.625)
+    return Workload(name="feo_sphere30_n512_f4", n=n, cell=box, n_z=n_z, dz=dz,
+                    lam=LAM_200KEV, sigma=interaction_constant(200e3, LAM_200KEV), f=f,
+                    alpha=0.020, beta=0.030, vproj=vproj, w=w, H=H,
+                    site_slice=lay[fe].astype(np.int32), site_x=x[fe].copy(),
+                    site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=scan)
+
+
 WORKLOADS = {
     "rocksalt_small": rocksalt_small,
     "rocksalt_fp32": rocksalt_fp32,
     "rocksalt_vacancy": rocksalt_vacancy,
     "nanoparticle": nanoparticle,
+    "nanoparticle_small": nanoparticle_small,
 }
 
 
