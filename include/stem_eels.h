@@ -161,16 +161,29 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 /* Context options.
  * EELS_OPT_ASSOCIATION selects how the tensor-core contraction groups the triple
  * product sum_p conj(S_out[d,p]) H_n[p] sum_j S_in[j,p] a_j(R) (Eq. SHn0 applied to
- * the probes): EELS_ASSOC_AUTO (default) picks, per call, the grouping with fewer
- * tensor-core flops over all sites; EELS_ASSOC_TRANSITION_FIRST forms
+ * the probes): EELS_ASSOC_AUTO (default) times both groupings once per contraction
+ * shape on the first slice that has sites and keeps the faster one for that shape in
+ * the context; EELS_ASSOC_TRANSITION_FIRST forms
  * M_n = S_out^H diag(H_n) S_in and then M_n a(R) (the paper's order);
  * EELS_ASSOC_PROBE_FIRST forms Y = S_in a(R) once per site (the elastic wave inside the
  * window) and then S_out^H (H_n . Y) per channel.  Both give the same map up to rounding.
+ *
+ * EELS_OPT_SHARD_COUNT (G >= 1, default 1) and EELS_OPT_SHARD_INDEX (0 <= g < G,
+ * default 0) restrict eels_inelastic_map to one shard of the detector beams: beam d
+ * (in the enumeration order of the aperture: rows q ascending, then p ascending)
+ * belongs to shard d mod G.  The map is a sum of |.|^2 over detector beams (Alg. 2,
+ * the detector sum of Eq. SHn0 applied to a probe), so the maps of the G shards add up
+ * to the full map; each shard needs the full S_in but only its share of S_out.  A shard
+ * with no beam returns a zero map.  eels_inelastic_map returns EELS_ERR_ARG if the
+ * index is not below the count.  The paper has no sharding; this serves one process per
+ * GPU, each computing one shard, with one FP64 sum of the maps at the end.
  * Returns EELS_ERR_ARG for an unknown option or value. */
 #define EELS_OPT_ASSOCIATION 1
 #define EELS_ASSOC_AUTO 0
 #define EELS_ASSOC_TRANSITION_FIRST 1
 #define EELS_ASSOC_PROBE_FIRST 2
+#define EELS_OPT_SHARD_COUNT 2
+#define EELS_OPT_SHARD_INDEX 3
 eels_status eels_set_option(eels_ctx* ctx, int option, int value);
 
 /* Per-kernel device timing.  While enabled, every kernel launch made by calls on

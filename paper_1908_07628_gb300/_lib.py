@@ -184,6 +184,12 @@ class Context:
         """Grouping of the tensor-core contraction (EELS_OPT_ASSOCIATION)."""
         self._check(self._lib.eels_set_option(self._h, 1, self.ASSOCIATIONS[how]), "set_option")
 
+    def set_detector_shard(self, index: int = 0, count: int = 1):
+        """Restrict inelastic_map to detector beams d with d % count == index
+        (EELS_OPT_SHARD_COUNT / EELS_OPT_SHARD_INDEX); (0, 1) is the whole aperture."""
+        self._check(self._lib.eels_set_option(self._h, 2, int(count)), "set_option")
+        self._check(self._lib.eels_set_option(self._h, 3, int(index)), "set_option")
+
     def profile_enable(self, on: bool = True):
         self._check(self._lib.eels_profile_enable(self._h, 1 if on else 0), "profile_enable")
 

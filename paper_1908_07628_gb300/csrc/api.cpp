@@ -20,6 +20,7 @@
 struct eels_ctx {
   int device = 0;
   int assoc = EELS_ASSOC_AUTO;
+  int shard_count = 1, shard_index = 0;   // detector-beam shard of eels_inelastic_map
   // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
   std::map<std::vector<int64_t>, int> assoc_cache;
   std::string err;
@@ -227,6 +228,16 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     if (value < EELS_ASSOC_AUTO || value > EELS_ASSOC_PROBE_FIRST)
       return fail(ctx, EELS_ERR_ARG, "unknown association");
     ctx->assoc = value;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_SHARD_COUNT) {
+    if (value < 1) return fail(ctx, EELS_ERR_ARG, "shard count must be >= 1");
+    ctx->shard_count = value;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_SHARD_INDEX) {
+    if (value < 0) return fail(ctx, EELS_ERR_ARG, "shard index must be >= 0");
+    ctx->shard_index = value;
     return EELS_OK;
   }
   return fail(ctx, EELS_ERR_ARG, "unknown option");
@@ -473,6 +484,22 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   if (dp.empty()) return fail(ctx, EELS_ERR_ARG, "no detector beam inside beta");
   if (!inside_band(n, f, dp, dq))
     return fail(ctx, EELS_ERR_ARG, "detector aperture extends beyond the band limit");
+  if (ctx->shard_index >= ctx->shard_count)
+    return fail(ctx, EELS_ERR_ARG, "shard index not below the shard count");
+  if (ctx->shard_count > 1) {   // keep beams d with d mod G == g
+    size_t k = 0;
+    for (size_t d = (size_t)ctx->shard_index; d < dp.size(); d += (size_t)ctx->shard_count, ++k) {
+      dp[k] = dp[d];
+      dq[k] = dq[d];
+    }
+    dp.resize(k);
+    dq.resize(k);
+    if (dp.empty()) {   // nothing of this shard: the map is zero
+      if (map_on_device) EELS_CK(cudaMemsetAsync(map_out, 0, sizeof(double) * n_map, st));
+      else std::memset(map_out, 0, sizeof(double) * n_map);
+      return EELS_OK;
+    }
+  }
   const int n_out = (int)dp.size();
   float2* tw = nullptr;
   if ((r = twiddles(ctx, n, &tw)) != EELS_OK) return r;

@@ -270,3 +270,37 @@ def test_shared_transition_potentials_equal_per_site_copies(g, ctx):
                                         wl.alpha, Hs, wl.site_slice, wl.win_x0, wl.win_y0,
                                         wl.site_x, wl.site_y, wl.scan, wl.beta)
     assert np.allclose(qa, qb, rtol=1e-12, atol=0)
+
+
+# --- detector-beam shards (the multi-GPU decomposition, run one after another) -------------
+
+def test_detector_shards_run_in_sequence_sum_to_the_full_map(g, ctx):
+    """G shards of the EELS aperture computed one after another on one GPU and added
+    on the host in shard order equal the full map; each shard equals the oracle's map
+    over the same detector beams."""
+    from paper_1908_07628_gb300 import shard
+    wl = _rand(128, 2, 16, n_sites=6, w=12)
+    n_out = ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)[0].size
+    sm = g.build_smatrix_for(ctx, wl)
+    try:
+        for prec, assoc in variants():
+            full = run_map(g, ctx, sm, wl, prec, assoc)
+            parts = []
+            for k in range(3):
+                ctx.set_detector_shard(k, 3)
+                parts.append(run_map(g, ctx, sm, wl, prec, assoc))
+            ctx.set_detector_shard(0, 1)
+            assert full.max() > 0 and eps(full, shard.sum_maps(parts)) < 1e-6, (prec, assoc)
+            if prec == "fp32":
+                for k in range(3):
+                    ref = lin.linear_map(wl, detectors=np.array(shard.detector_shard(n_out, k, 3)))
+                    assert eps(ref, parts[k]) < EPS_FP32, k
+        # more shards than detector beams: the surplus shards are empty
+        ctx.set_detector_shard(n_out + 1, n_out + 2)
+        assert not g.inelastic_map_for(ctx, sm, wl, "tf32").any()
+        ctx.set_detector_shard(3, 3)
+        with pytest.raises(g.EelsError) as e:
+            g.inelastic_map_for(ctx, sm, wl, "fp32")
+        assert e.value.status == 1
+    finally:
+        ctx.set_detector_shard(0, 1)
