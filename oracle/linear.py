@@ -65,22 +65,77 @@ def build_s_in(wl):
     return out, beams
 
 
-def iter_s_out(wl):
+def _exit_detector_waves(wl, detectors):
+    """beta_d(n_z-1) = F^-1 conj(P) F |k_d> for the EELS aperture's beams, and P."""
+    n, L, f = wl.n, wl.cell, wl.f
+    det = ms.lattice_beams(n, L, wl.lam, f, wl.beta)
+    if detectors is not None:
+        det = (det[0][detectors], det[1][detectors])
+    P = ms.propagator(n, L, wl.lam, wl.dz)
+    return np.fft.ifft2(np.conj(P)[None] * np.fft.fft2(plane_waves(n, det, f))), P
+
+
+def _back_one_slice(beta, wl, P, i):
+    """beta(i-1) = F^-1 conj(P) F (conj(t_i) beta(i)): one slice towards the entrance."""
+    t = ms.transmission(wl.vproj[i], wl.sigma)
+    return np.fft.ifft2(np.conj(P)[None] * np.fft.fft2(np.conj(t)[None] * beta))
+
+
+def iter_s_out(wl, detectors=None):
     """Yield (i, Sout_i) for i = n_z-1 .. 0 with Sout_i = 4 Dec(beta_d(i)).
 
     beta_d(n_z-1) = F^-1 conj(P) F |k_d>;  beta_d(i-1) = F^-1 conj(P) F (conj(t_i) beta_d(i)),
     i.e. the detector plane waves carried back through slices n_z-1 .. i+1 and the
-    propagation half of slice i.
+    propagation half of slice i.  `detectors` (indices into the aperture's beam
+    list) keeps only those detector beams.
     """
-    n, L, f = wl.n, wl.cell, wl.f
-    det = ms.lattice_beams(n, L, wl.lam, f, wl.beta)
-    P = ms.propagator(n, L, wl.lam, wl.dz)
-    beta = np.fft.ifft2(np.conj(P)[None] * np.fft.fft2(plane_waves(n, det, f)))
+    beta, P = _exit_detector_waves(wl, detectors)
     for i in range(wl.n_z - 1, -1, -1):
         yield i, 4.0 * ms.decimate(beta)
         if i > 0:
-            t = ms.transmission(wl.vproj[i], wl.sigma)
-            beta = np.fft.ifft2(np.conj(P)[None] * np.fft.fft2(np.conj(t)[None] * beta))
+            beta = _back_one_slice(beta, wl, P, i)
+
+
+def iter_s_out_recompute(wl, detectors=None):
+    """Yield (i, Sout_i) for i = 0 .. n_z-1, S_2 recalculated from the exit surface
+    for every slice (Sec. III second listing, "Re-calculate S_2"): n_z - 1 - i
+    backward slice steps for depth i.  Exact; equal to iter_s_out."""
+    start, P = _exit_detector_waves(wl, detectors)
+    for i in range(wl.n_z):
+        beta = start
+        for j in range(wl.n_z - 1, i, -1):
+            beta = _back_one_slice(beta, wl, P, j)
+        yield i, 4.0 * ms.decimate(beta)
+
+
+def iter_s_out_inverse(wl, detectors=None):
+    """Yield (i, Sout_i) for i = 0 .. n_z-1 with S_2 carried back to depth 0 once and
+    then retreated one slice per depth with the inverse multislice operator
+    (Sec. IV C, Eq. MSinvop).
+
+    The backward step is beta(i) = G(conj(t_{i+1}) beta(i+1)) with G = F^-1 conj(P) F.
+    Its inverse undoes the last operation first, with the conjugated factors:
+    propagate with P, then multiply by t_{i+1}.  Both are exact on the band, but
+    conj(t) beta carries content outside the band limit that G removed, and the
+    inverse cannot restore it (the loss Sec. IV C describes); the retreated wave is
+    projected onto the band, the space the S-matrices represent:
+
+        beta~(0) = beta(0),   beta~(i+1) = B . F[t_{i+1} F^-1[P F beta~(i)]]  (in k).
+    """
+    beta, P = _exit_detector_waves(wl, detectors)
+    for i in range(wl.n_z - 1, 0, -1):
+        beta = _back_one_slice(beta, wl, P, i)
+    B = ms.band_limit(wl.n)
+    for i in range(wl.n_z):
+        yield i, 4.0 * ms.decimate(beta)
+        if i + 1 < wl.n_z:
+            t = ms.transmission(wl.vproj[i + 1], wl.sigma)
+            moved = t[None] * np.fft.ifft2(P[None] * np.fft.fft2(beta))
+            beta = np.fft.ifft2(B[None] * np.fft.fft2(moved))
+
+
+S_OUT_SCHEMES = {"stream": iter_s_out, "recompute": iter_s_out_recompute,
+                 "inverse": iter_s_out_inverse}
 
 
 def probe_coefficients(wl, beams, rx, ry) -> np.ndarray:
@@ -92,8 +147,13 @@ def probe_coefficients(wl, beams, rx, ry) -> np.ndarray:
     return c * np.exp(1j * ph)
 
 
-def linear_map(wl, s_in=None):
-    """PRISM-EELS map, FP64: I float64 [n_types][n_sy][n_sx]."""
+def linear_map(wl, s_in=None, detectors=None, scheme="stream"):
+    """PRISM-EELS map, FP64: I float64 [n_types][n_sy][n_sx].
+
+    With `detectors` (indices into the EELS aperture's beam list) the detector sum
+    of Eq. SHn0 runs over those beams only.  `scheme` picks how S_out reaches each
+    depth: "stream" (backwards once), "recompute" (from the exit surface for every
+    slice) or "inverse" (retreated with the inverse multislice operator)."""
     n, L, f = wl.n, wl.cell, wl.f
     nh = n // 2
     if s_in is None:
@@ -104,7 +164,7 @@ def linear_map(wl, s_in=None):
     a = probe_coefficients(wl, beams, rx, ry)
     T = wl.n_types
     I = np.zeros((T, wl.scan[1], wl.scan[0]))
-    for i, sout in iter_s_out(wl):
+    for i, sout in S_OUT_SCHEMES[scheme](wl, detectors):
         for s in np.nonzero(wl.site_slice == i)[0]:
             okx = ms.axis_in_window(wl.site_x[s], rx, L, f)
             oky = ms.axis_in_window(wl.site_y[s], ry, L, f)

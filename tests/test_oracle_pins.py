@@ -221,6 +221,64 @@ def test_linear_algorithm_adds_no_error(n, f, cell, alpha, beta, seed):
     assert ms.relative_error(Iq, Il) < 1e-12
 
 
+# --- S_2 schemes of Alg. 2: recalculated per slice (Sec. III), inverse multislice (Sec. IV C)
+
+@pytest.mark.parametrize("n,f,cell,seed", [(32, 1, 6.0, 1), (64, 2, 12.0, 2)])
+def test_recalculated_s2_reproduces_the_conventional_map(n, f, cell, seed):
+    """The listing recalculates S_2 from the exit surface at every slice: exact."""
+    wl = _tiny(n=n, f=f, cell=cell, alpha=0.02, beta=0.03, seed=seed, n_z=4, n_sites=6, w=8,
+               scan_n=3)
+    Iq = ms.quadratic_map(wl)
+    assert Iq.max() > 0
+    assert ms.relative_error(Iq, lin.linear_map(wl, scheme="recompute")) < 1e-12
+
+
+def test_inverse_multislice_is_exact_in_free_space():
+    """With v = 0 nothing leaves the band, so the retreat undoes the backward step."""
+    wl = _tiny(n=32, f=1, cell=6.0, alpha=0.02, beta=0.03, seed=6, n_z=4, n_sites=6, w=8)
+    wl.vproj = np.zeros_like(wl.vproj)
+    Iq = ms.quadratic_map(wl)
+    assert Iq.max() > 0
+    assert ms.relative_error(Iq, lin.linear_map(wl, scheme="inverse")) < 1e-12
+
+
+def test_inverse_multislice_is_exact_at_the_entrance_slice():
+    """S_2 at depth 0 comes from the full backward sweep; only deeper slices are retreated."""
+    wl = _tiny(n=32, f=1, cell=6.0, alpha=0.02, beta=0.03, seed=7, n_z=4, n_sites=6, w=8)
+    wl.vproj = (wl.vproj * 4.0).astype(np.float32)        # strong scattering
+    first = wl.with_sites(np.arange(wl.n_sites))
+    first.site_slice[:] = 0
+    Iq = ms.quadratic_map(first)
+    assert ms.relative_error(Iq, lin.linear_map(first, scheme="inverse")) < 1e-12
+    deep = wl.with_sites(np.arange(wl.n_sites))
+    deep.site_slice[:] = wl.n_z - 1
+    Iq = ms.quadratic_map(deep)
+    assert ms.relative_error(Iq, lin.linear_map(deep, scheme="inverse")) > 1e-4
+
+
+def test_inverse_multislice_is_exact_while_the_waves_stay_in_band():
+    """Slices of weak single-harmonic potentials v_i = A cos(2 pi (a_i x + b_i y)/L + phi_i)
+    with sigma A = 0.1: t_i has harmonics of order m with weight ~ J_m(0.1), and reaching
+    the band edge from the small apertures needs six orders (~1e-11).  The retreat must
+    then reproduce the conventional map, which requires the transmission of the right
+    slice at every retreat step (the potentials change the map by far more than 1e-6)."""
+    n, cell = 32, 8.0
+    wl = _tiny(n=n, f=1, cell=cell, alpha=0.008, beta=0.008, seed=8, n_z=4, n_sites=6, w=8,
+               scan_n=3)
+    x = np.arange(n) * cell / n
+    amp = 0.1 / wl.sigma
+    freqs = [(1, 0, 0.3), (0, 1, 1.7), (1, 1, 2.9), (1, -1, 4.1)]
+    v = np.empty((wl.n_z, n, n))
+    for i, (a, b, ph) in enumerate(freqs):
+        v[i] = amp * np.cos(2 * math.pi * (a * x[None, :] + b * x[:, None]) / cell + ph)
+    wl.vproj = v.astype(np.float32)
+    Iq = ms.quadratic_map(wl)
+    assert ms.relative_error(Iq, lin.linear_map(wl, scheme="inverse")) < 1e-6
+    free = wl.with_sites(np.arange(wl.n_sites))
+    free.vproj = np.zeros_like(wl.vproj)
+    assert ms.relative_error(Iq, ms.quadratic_map(free)) > 1e-2
+
+
 def test_linear_equals_quadratic_on_rocksalt_probes():
     wl = sp.rocksalt_small()
     pos = [(0, 0), (3, 5), (7, 2)]
