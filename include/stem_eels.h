@@ -184,6 +184,23 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 #define EELS_ASSOC_PROBE_FIRST 2
 #define EELS_OPT_SHARD_COUNT 2
 #define EELS_OPT_SHARD_INDEX 3
+/* EELS_OPT_SOUT_SCHEME selects how eels_inelastic_map brings the detector-side
+ * matrix S_out (the paper's S_2) to each depth; S_in always comes from the handle.
+ *   EELS_SOUT_STREAM (default): carried backwards from the exit surface once, the
+ *     contraction of each depth running as the sweep passes it; exact, n_z n_out
+ *     beam-steps.
+ *   EELS_SOUT_RECOMPUTE: recalculated from the exit surface for every depth that holds
+ *     transitions, as the Sec. III listing does ("Re-calculate S_2"); exact, up to
+ *     n_z (n_z + 1)/2 n_out beam-steps.
+ *   EELS_SOUT_INVERSE: carried back to depth 0 once, then retreated one slice per depth
+ *     with the inverse multislice operator (Sec. IV C, Eq. MSinvop): propagate with P,
+ *     multiply by t_{i+1}, project onto the band.  Approximate: what the backward sweep
+ *     scattered outside the band limit is not recovered; exact at depth 0 and in free
+ *     space.  2 n_z n_out beam-steps plus one band projection per depth. */
+#define EELS_OPT_SOUT_SCHEME 4
+#define EELS_SOUT_STREAM 0
+#define EELS_SOUT_RECOMPUTE 1
+#define EELS_SOUT_INVERSE 2
 eels_status eels_set_option(eels_ctx* ctx, int option, int value);
 
 /* Per-kernel device timing.  While enabled, every kernel launch made by calls on

@@ -190,6 +190,13 @@ class Context:
         self._check(self._lib.eels_set_option(self._h, 2, int(count)), "set_option")
         self._check(self._lib.eels_set_option(self._h, 3, int(index)), "set_option")
 
+    SOUT_SCHEMES = {"stream": 0, "recompute": 1, "inverse": 2}
+
+    def set_sout_scheme(self, how: str = "stream"):
+        """How S_out reaches each depth (EELS_OPT_SOUT_SCHEME): "stream", "recompute"
+        (the Sec. III listing) or "inverse" (inverse multislice, Sec. IV C)."""
+        self._check(self._lib.eels_set_option(self._h, 4, self.SOUT_SCHEMES[how]), "set_option")
+
     def profile_enable(self, on: bool = True):
         self._check(self._lib.eels_profile_enable(self._h, 1 if on else 0), "profile_enable")
 

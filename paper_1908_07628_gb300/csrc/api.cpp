@@ -21,6 +21,7 @@ struct eels_ctx {
   int device = 0;
   int assoc = EELS_ASSOC_AUTO;
   int shard_count = 1, shard_index = 0;   // detector-beam shard of eels_inelastic_map
+  int sout_scheme = EELS_SOUT_STREAM;     // how S_out reaches each depth
   // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
   std::map<std::vector<int64_t>, int> assoc_cache;
   std::string err;
@@ -228,6 +229,12 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     if (value < EELS_ASSOC_AUTO || value > EELS_ASSOC_PROBE_FIRST)
       return fail(ctx, EELS_ERR_ARG, "unknown association");
     ctx->assoc = value;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_SOUT_SCHEME) {
+    if (value < EELS_SOUT_STREAM || value > EELS_SOUT_INVERSE)
+      return fail(ctx, EELS_ERR_ARG, "unknown S_out scheme");
+    ctx->sout_scheme = value;
     return EELS_OK;
   }
   if (option == EELS_OPT_SHARD_COUNT) {
@@ -714,13 +721,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     }
     return EELS_OK;
   };
-  for (int i = n_z - 1; i >= 0; --i) {
-    // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
-    {
-      Prof pr(ctx, "row_pass_adjoint", st);
-      EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, sm->t + (int64_t)i * n * n, 1, 2, Sout.p, n_out,
-                              plane, i > 0 ? 1 : 0, tw, st));
-    }
+  // contraction of depth i (S_out(i) in Sout) into the map
+  auto contract_depth = [&](int i) -> eels_status {
     const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
     if (tc && site_off[i + 1] > site_off[i]) {
       int pf = chosen == EELS_ASSOC_PROBE_FIRST ? 1 : 0;
@@ -769,10 +771,95 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
                                              sc->n_sy, tb, wl, dmap.p, st));
       }
     }
-    if (i > 0) {
-      Prof pr(ctx, "col_pass_adjoint", st);
-      EELS_CK(launch_col_pass(n, n_out, Phi.p, W.p, sm->ptab, 1, 0, nullptr, nullptr, nullptr, 0.0,
-                              tw, st));
+    return EELS_OK;
+  };
+  const auto t_of = [&](int i) { return sm->t + (int64_t)i * n * n; };
+  const auto has_work = [&](int i) { return slice_off[i + 1] > slice_off[i]; };
+  // one backward slice step of the detector waves in `from` (row-spectrum form):
+  // conj(t_i), x-FFT, then y-FFT, conj(P), inverse y-FFT into `to`
+  auto back_step = [&](float2* from, float2* tmp, int i) -> eels_status {
+    {
+      Prof pr(ctx, "row_pass_adjoint", st);
+      EELS_CK(launch_row_pass(n, n_out, from, tmp, t_of(i), 1, 0, nullptr, 0, 0, 1, tw, st));
+    }
+    Prof pr(ctx, "col_pass_adjoint", st);
+    EELS_CK(launch_col_pass(n, n_out, tmp, from, sm->ptab, 1, 0, nullptr, nullptr, nullptr, 0.0,
+                            tw, st));
+    return EELS_OK;
+  };
+  // S_out(i) = N Dec(wave) of the waves in `from`, nothing else
+  auto store_sout = [&](const float2* from, int i) -> eels_status {
+    Prof pr(ctx, "row_pass_store", st);
+    EELS_CK(launch_row_pass(n, n_out, from, nullptr, t_of(i), 1, 2, Sout.p, n_out, plane, 0, tw,
+                            st));
+    return EELS_OK;
+  };
+
+  eels_status rs = EELS_OK;
+  if (ctx->sout_scheme == EELS_SOUT_STREAM) {
+    // S_out streamed backwards once (Alg. 2 with the slice loop run from the exit)
+    for (int i = n_z - 1; i >= 0; --i) {
+      // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
+      {
+        Prof pr(ctx, "row_pass_adjoint", st);
+        EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, t_of(i), 1, 2, Sout.p, n_out, plane,
+                                i > 0 ? 1 : 0, tw, st));
+      }
+      if ((rs = contract_depth(i)) != EELS_OK) return rs;
+      if (i > 0) {
+        Prof pr(ctx, "col_pass_adjoint", st);
+        EELS_CK(launch_col_pass(n, n_out, Phi.p, W.p, sm->ptab, 1, 0, nullptr, nullptr, nullptr,
+                                0.0, tw, st));
+      }
+    }
+  } else if (ctx->sout_scheme == EELS_SOUT_RECOMPUTE) {
+    // Alg. 2 as listed: S_2 recalculated from the exit surface for every depth
+    for (int i = 0; i < n_z; ++i) {
+      if (!has_work(i)) continue;
+      {
+        Prof pr(ctx, "init_plane_waves", st);
+        EELS_CK(eels::launch_init_plane_waves(W.p, n, n_out, dpx.p, dpy.p, damp.p, tw, st));
+      }
+      for (int j = n_z - 1; j > i; --j)
+        if ((rs = back_step(W.p, Phi.p, j)) != EELS_OK) return rs;
+      if ((rs = store_sout(W.p, i)) != EELS_OK) return rs;
+      if ((rs = contract_depth(i)) != EELS_OK) return rs;
+    }
+  } else {
+    // Sec. IV C: S_2 carried back to depth 0 once, then retreated one slice per depth
+    // with the inverse step (P, then t_{i+1}) and projected onto the band
+    // scales: a column pass multiplies by N x its table, a row pass by N; the retreat
+    // starts from a wave at true scale, so col(P / N^2) -> 1/N, row -> 1, and the band
+    // table carries 1/N to end at true scale again
+    DevBuf<float2> mtab;
+    EELS_CK(mtab.alloc((size_t)plane, st));
+    EELS_CK(eels::launch_propagator_table(mtab.p, n, sm->cell, sm->lam, 0.0,
+                                          (float)(1.0 / (double)n), st));
+    float2* cur = W.p;
+    float2* oth = Phi.p;
+    for (int j = n_z - 1; j > 0; --j)
+      if ((rs = back_step(cur, oth, j)) != EELS_OK) return rs;
+    for (int i = 0; i < n_z; ++i) {
+      if (has_work(i)) {
+        if ((rs = store_sout(cur, i)) != EELS_OK) return rs;
+        if ((rs = contract_depth(i)) != EELS_OK) return rs;
+      }
+      if (i + 1 == n_z) break;
+      {
+        Prof pr(ctx, "col_pass_inverse", st);
+        EELS_CK(launch_col_pass(n, n_out, cur, oth, sm->ptab, 0, 0, nullptr, nullptr, nullptr,
+                                0.0, tw, st));
+      }
+      {
+        Prof pr(ctx, "row_pass_inverse", st);
+        EELS_CK(launch_row_pass(n, n_out, oth, cur, t_of(i + 1), 0, 0, nullptr, 0, 0, 1, tw, st));
+      }
+      {
+        Prof pr(ctx, "col_pass_band", st);
+        EELS_CK(launch_col_pass(n, n_out, cur, oth, mtab.p, 0, 0, nullptr, nullptr, nullptr, 0.0,
+                                tw, st));
+      }
+      std::swap(cur, oth);
     }
   }
   // I = f^2 (f^2/n_in) (4/N^2)^2 sum |M_gpu a_gpu|^2: S-matrices are stored scaled

@@ -304,3 +304,56 @@ def test_detector_shards_run_in_sequence_sum_to_the_full_map(g, ctx):
         assert e.value.status == 1
     finally:
         ctx.set_detector_shard(0, 1)
+
+
+# --- S_out schemes: the Sec. III listing and the inverse multislice retreat (Sec. IV C) ----
+
+def _coarse(n, f, seed):
+    """Strong random potentials sampled at 0.2 A: t_i reaches the band limit, so the
+    inverse retreat loses a visible part of the detector waves."""
+    return sp.random_workload(n=n, n_z=5, f=f, cell=n * 0.2, n_sites=8, w=12, seed=seed,
+                              scan_n=3, alpha=0.0165, beta=0.025, dz=1.8, vscale=1200.0)
+
+
+@pytest.mark.parametrize("scheme,n,f,seed", [("recompute", 128, 2, 17), ("inverse", 64, 2, 18),
+                                             ("inverse", 128, 2, 26)])
+def test_sout_schemes_match_oracle(g, ctx, scheme, n, f, seed):
+    wl = _coarse(n, f, seed)
+    ref = lin.linear_map(wl, scheme=scheme)
+    exact = lin.linear_map(wl)
+    assert exact.max() > 0
+    if scheme == "inverse":
+        assert eps(exact, ref) > 1e-3                   # the approximation is visible
+    sm = g.build_smatrix_for(ctx, wl)
+    ctx.set_sout_scheme(scheme)
+    try:
+        for prec, assoc in variants():
+            got = run_map(g, ctx, sm, wl, prec, assoc)
+            assert eps(ref, got) < EPS[prec], (prec, assoc, eps(ref, got))
+    finally:
+        ctx.set_sout_scheme("stream")
+
+
+def test_inverse_scheme_on_rocksalt_matches_oracle(g, ctx):
+    wl = sp.rocksalt_small()
+    ref = lin.linear_map(wl, scheme="inverse")
+    sm = g.build_smatrix_for(ctx, wl)
+    ctx.set_sout_scheme("inverse")
+    try:
+        got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    finally:
+        ctx.set_sout_scheme("stream")
+    assert eps(ref, got) < EPS_FP32
+
+
+def test_inverse_scheme_is_exact_in_free_space(g, ctx):
+    wl = _rand(128, 2, 20, n_sites=6, w=10, n_z=4)
+    wl.vproj = np.zeros_like(wl.vproj)
+    sm = g.build_smatrix_for(ctx, wl)
+    exact = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    ctx.set_sout_scheme("inverse")
+    try:
+        got = g.inelastic_map_for(ctx, sm, wl, "fp32")
+    finally:
+        ctx.set_sout_scheme("stream")
+    assert exact.max() > 0 and eps(exact, got) < 1e-5
