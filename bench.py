@@ -180,9 +180,56 @@ def _algorithmic(wl, n_in, n_out, prof):
     # row pass: read W + write Phi (n x n/2 per wave), store n/2 x n/2 per wave, read t once
     for name, waves in (("row_pass", n_in), ("row_pass_adjoint", n_out)):
         out[name] = ("hbm", waves * (2 * n * nh + nh * nh) * cplx + n * n * cplx)
-    for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out)):
+    out["row_pass_inverse"] = ("hbm", n_out * 2 * n * nh * cplx + n * n * cplx)
+    out["row_pass_store"] = ("hbm", n_out * (n * nh + nh * nh) * cplx)
+    for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out),
+                        ("col_pass_inverse", n_out), ("col_pass_band", n_out)):
         out[name] = ("hbm", waves * 2 * n * nh * cplx)
     return out
+
+
+def s2_study(g, ctx, stream, thickness_cells=(5, 12, 19, 23), reps=2):
+    """Sec. IV C trade-off on a rocksalt thickness series (8x8 cells, 256^2, f = 2, 16x16
+    scan): map time of each S_out scheme (TF32 contraction) and the error of the
+    inverse retreat against the exact stream (FP32 contraction, so that the scheme's
+    error is not hidden under tensor-core rounding)."""
+    import torch
+    rows = []
+    for nzc in thickness_cells:
+        wl = sp.rocksalt_slab(nzc)
+        vdev = torch.from_numpy(wl.vproj).cuda()
+        Hdev = torch.from_numpy(wl.H).cuda()
+        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
+        ms_, maps = {}, {}
+        for scheme in ("stream", "recompute", "inverse"):
+            ctx.set_sout_scheme(scheme)
+            maps[scheme] = g.inelastic_map_for(ctx, sm, wl, "fp32", H=Hdev, stream=stream)
+            g.inelastic_map_for(ctx, sm, wl, "tf32", H=Hdev, stream=stream)   # warm / tune
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                g.inelastic_map_for(ctx, sm, wl, "tf32", H=Hdev, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_[scheme] = e0.elapsed_time(e1) / reps
+        ctx.set_sout_scheme("stream")
+        sm.free()
+        ref = maps["stream"]
+
+        def err(m):
+            return float(np.sqrt(np.sum((m - ref) ** 2) / np.sum(ref ** 2)))
+        rows.append({"thickness_A": round(wl.n_z * wl.dz, 1), "n_z": wl.n_z,
+                     "map_ms": {k: round(v, 2) for k, v in ms_.items()},
+                     "eps_inverse_vs_exact": err(maps["inverse"]),
+                     "eps_recompute_vs_exact": err(maps["recompute"]),
+                     "inverse_speedup_vs_recompute_pct":
+                         round(100.0 * (ms_["recompute"] / ms_["inverse"] - 1.0), 1),
+                     "stream_speedup_vs_inverse_pct":
+                         round(100.0 * (ms_["inverse"] / ms_["stream"] - 1.0), 1)})
+    return {"workload": "rocksalt Fe-O 8x8 cells x thickness, 256^2, f=2, 16x16 scan",
+            "rows": rows}
 
 
 def _source_hash(kernel):
@@ -223,6 +270,7 @@ def gpu_arm(args, rank, world):
     wl = load_workload(args)
     ctx = g.Context(dev)
     ctx.set_association(args.association)
+    ctx.set_sout_scheme(args.sout_scheme)
     stream = torch.cuda.current_stream()
     vdev = torch.from_numpy(wl.vproj).cuda()
     Hdev = torch.from_numpy(wl.H).cuda()
@@ -538,6 +586,10 @@ def main():
     ap.add_argument("--quad-probes", type=int, default=8)
     ap.add_argument("--association", default="auto",
                     choices=["auto", "transition_first", "probe_first"])
+    ap.add_argument("--sout-scheme", default="stream", choices=["stream", "recompute", "inverse"],
+                    help="how S_out reaches each depth (the paper's S_2 variants)")
+    ap.add_argument("--s2-study", action="store_true",
+                    help="print the S_out scheme thickness study instead of the bench line")
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")
@@ -577,6 +629,16 @@ def main():
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
                           "config": {"workload": "mixed map request stream (seed 4)"}}))
+        return
+    if args.s2_study:
+        import torch
+        from paper_1908_07628_gb300 import build
+        build.build()
+        import paper_1908_07628_gb300 as g
+        ctx = g.Context(0)
+        res = s2_study(g, ctx, torch.cuda.current_stream())
+        print(json.dumps({"study": "S_out schemes (Sec. III listing, Sec. IV C inverse multislice)",
+                          "data": "synthetic", **res}))
         return
     line = gpu_arm(args, rank, world)
     line["cpu_baseline"] = cpu

@@ -276,6 +276,13 @@ def rocksalt_fp32():
                              scan_n=32)
 
 
+def rocksalt_slab(nzc: int, n: int = 256, ncell: int = 8, f: int = 2, scan_n: int = 16):
+    """Rocksalt Fe-O ncell x ncell x nzc cells (2 nzc slices of a/2), n^2 grid, a scan of
+    scan_n^2 over the central cell: the thickness series of the S_2 scheme study."""
+    return _crystal_workload(f"rocksalt_{ncell}x{ncell}x{nzc}_n{n}_f{f}", n=n, ncell=ncell,
+                             nzc=nzc, f=f, w=32, scan_n=scan_n)
+
+
 def rocksalt_vacancy():
     """Rocksalt Fe-O 12x12x40 cells, 768^2 grid, 80 slices, f=2, 5% Fe vacancies (seed 3)."""
     return _crystal_workload("rocksalt_12x12x40_n768_f2_vac5", n=768, ncell=12, nzc=40, f=2,
