@@ -146,6 +146,36 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
                                const eels_scan* scan, double beta, int precision,
                                double* map_out, int map_on_device, void* stream);
 
+/* Elastic STEM images from the same S-matrix (Sec. IV D: the annular dark-field image
+ * with a 60 mrad inner angle and the incoherent bright-field image whose detector has
+ * the extent of the EELS aperture, by which the EELS map is divided).
+ *
+ * Needs a handle built while EELS_OPT_EXIT_PLANE was 1 (S_in at the exit surface);
+ * otherwise EELS_ERR_ARG.  For probe R the exit wave sum_j c a_j(R) S_exit[j] (Sec. III)
+ * is cut to the L/f cell around R on the N/2 grid: the M = N/(2f) pixels per axis whose
+ * minimum-image offset from R lies in [-L/2f, L/2f) (the rule of the site windows),
+ * starting at the in-rule pixel whose cyclic predecessor is out of rule (pixel 0 at f = 1).
+ * Detector d integrates over the cut's DFT lattice k = f(a, b)/L:
+ *   out[d][iy][ix] = (16 f^2 / N^2) sum_{k in D_d} |sum_{p in cut} psi(x_p) e^{-2 pi i k.x_p}|^2
+ * with D_d = {k : inner_d <= lambda |k| (<= outer_d if outer_d > 0), 16 f^2 (a^2 + b^2) < N^2}.
+ * For a wave that lies inside the cut this is the EELS detector's f^2 sum over f-lattice
+ * beams.  1 <= n_det <= 8.  out is FP64 [n_det][n_sy][n_sx], caller-owned, host or device
+ * (out_on_device), overwritten.  EELS_ERR_UNSUPPORTED if N/2 is not divisible by f or
+ * M is not one of 16, 32, 48, 64, 96, 128, 192, 256, 384, 512. */
+typedef struct {
+  double inner;   /* semi-angle (rad), lambda |k| >= inner */
+  double outer;   /* semi-angle (rad), lambda |k| <= outer; <= 0: up to the band limit */
+} eels_detector;
+eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eels_scan* scan,
+                                const eels_detector* detectors, int n_det, double* out,
+                                int out_on_device, void* stream);
+
+/* The bright-field correction of Sec. IV D: map[m][p] /= bf[p] in place for every
+ * channel m < n_types and pixel p < n_pix (FP64; both host or both device per
+ * on_device; a zero bright-field pixel gives inf or nan there, as IEEE division does). */
+eels_status eels_divide_map(eels_ctx* ctx, double* map, const double* bf, int n_types,
+                            int64_t n_pix, int on_device, void* stream);
+
 /* The conventional quadratic algorithm (Sec. III first listing) on the GPU,
  * batched over probes and inelastic waves, same FFT kernels.  If positions is
  * non-NULL only the n_pos scan points positions[2k] = iy, positions[2k+1] = ix
@@ -197,6 +227,10 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  *     multiply by t_{i+1}, project onto the band.  Approximate: what the backward sweep
  *     scattered outside the band limit is not recovered; exact at depth 0 and in free
  *     space.  2 n_z n_out beam-steps plus one band projection per depth. */
+/* EELS_OPT_EXIT_PLANE (0 default, 1): eels_build_smatrix also stores S_in at the exit
+ * surface (one more depth of n_in N/2 x N/2 planes and one more half slice step), which
+ * eels_elastic_images needs. */
+#define EELS_OPT_EXIT_PLANE 5
 #define EELS_OPT_SOUT_SCHEME 4
 #define EELS_SOUT_STREAM 0
 #define EELS_SOUT_RECOMPUTE 1

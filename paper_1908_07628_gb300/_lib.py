@@ -60,6 +60,10 @@ class ServerStats(C.Structure):
                 ("pixel_slices_per_s", C.c_double), ("peak_bytes", C.c_int64)]
 
 
+class Detector(C.Structure):
+    _fields_ = [("inner", C.c_double), ("outer", C.c_double)]
+
+
 EXPORTS = {
     "eels_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
     "eels_destroy": (None, [C.c_void_p]),
@@ -78,6 +82,11 @@ EXPORTS = {
                                                C.POINTER(Transitions), C.POINTER(Scan), C.c_double,
                                                C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                                C.c_void_p, C.POINTER(C.c_int64)]),
+    "eels_elastic_images": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Scan),
+                                      C.POINTER(Detector), C.c_int, C.c_void_p, C.c_int,
+                                      C.c_void_p]),
+    "eels_divide_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
+                                  C.c_int, C.c_void_p]),
     "eels_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
@@ -189,6 +198,42 @@ class Context:
         (EELS_OPT_SHARD_COUNT / EELS_OPT_SHARD_INDEX); (0, 1) is the whole aperture."""
         self._check(self._lib.eels_set_option(self._h, 2, int(count)), "set_option")
         self._check(self._lib.eels_set_option(self._h, 3, int(index)), "set_option")
+
+    def set_exit_plane(self, on: bool = True):
+        """Builds also keep S_in at the exit surface (EELS_OPT_EXIT_PLANE), for elastic_images."""
+        self._check(self._lib.eels_set_option(self._h, 5, 1 if on else 0), "set_option")
+
+    def elastic_images(self, sm, scan, detectors, out=None, stream=None):
+        """Elastic images [n_det][n_sy][n_sx] (FP64) for detectors [(inner, outer), ...]
+        (semi-angles in rad; outer <= 0: up to the band limit)."""
+        dets = (Detector * len(detectors))(*[Detector(float(a), float(b)) for a, b in detectors])
+        sc = Scan(*[int(v) for v in scan[:2]], *[float(v) for v in scan[2:]])
+        shape = (len(detectors), int(scan[1]), int(scan[0]))
+        out_arr = np.zeros(shape) if out is None else out
+        o, o_dev, okeep = _ptr(out_arr, np.float64)
+        st = self._lib.eels_elastic_images(self._h, sm._h, C.byref(sc), dets, len(detectors), o,
+                                           o_dev, _stream(stream))
+        self._check(st, "eels_elastic_images")
+        if out is None or not o_dev:
+            if o_dev == 0 and out is not None and okeep is not out:
+                out[...] = okeep
+            return okeep if out is None else out
+        return out
+
+    def divide_map(self, eels_map, bf, stream=None):
+        """In place: eels_map[m] /= bf (the bright-field correction); both numpy FP64
+        arrays or both CUDA FP64 tensors.  Returns eels_map."""
+        m_ptr, m_dev, mkeep = _ptr(eels_map, np.float64)
+        b_ptr, b_dev, bkeep = _ptr(bf, np.float64)
+        if m_dev != b_dev:
+            raise ValueError("map and bright field must both be on the host or the device")
+        n_pix = int(bf.shape[-1] * bf.shape[-2])
+        st = self._lib.eels_divide_map(self._h, m_ptr, b_ptr, int(eels_map.shape[0]), n_pix, m_dev,
+                                       _stream(stream))
+        self._check(st, "eels_divide_map")
+        if not m_dev and mkeep is not eels_map:
+            eels_map[...] = mkeep
+        return eels_map
 
     SOUT_SCHEMES = {"stream": 0, "recompute": 1, "inverse": 2}
 

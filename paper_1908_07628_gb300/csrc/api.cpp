@@ -22,6 +22,7 @@ struct eels_ctx {
   int assoc = EELS_ASSOC_AUTO;
   int shard_count = 1, shard_index = 0;   // detector-beam shard of eels_inelastic_map
   int sout_scheme = EELS_SOUT_STREAM;     // how S_out reaches each depth
+  bool keep_exit = false;                 // builds also store S_in at the exit surface
   // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
   std::map<std::vector<int64_t>, int> assoc_cache;
   std::string err;
@@ -42,6 +43,7 @@ struct eels_smatrix {
   float2* t = nullptr;         // [n_z][n][n]
   float2* ptab = nullptr;      // [n/2][n/2] box order, forward propagator / N^2
   float2* s_in = nullptr;      // [n_z][n_in][n/2][n/2]
+  float2* s_exit = nullptr;    // [n_in][n/2][n/2] exit surface, N Dec(psi_j(n_z)), or null
   cudaStream_t st = nullptr;   // stream the handle's memory is ordered on
 };
 
@@ -237,6 +239,11 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     ctx->sout_scheme = value;
     return EELS_OK;
   }
+  if (option == EELS_OPT_EXIT_PLANE) {
+    if (value != 0 && value != 1) return fail(ctx, EELS_ERR_ARG, "exit plane option is 0 or 1");
+    ctx->keep_exit = value == 1;
+    return EELS_OK;
+  }
   if (option == EELS_OPT_SHARD_COUNT) {
     if (value < 1) return fail(ctx, EELS_ERR_ARG, "shard count must be >= 1");
     ctx->shard_count = value;
@@ -348,7 +355,10 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
       (e = cudaMallocAsync((void**)&sm->ptab, sizeof(float2) * (size_t)plane, st)) != cudaSuccess ||
       (e = cudaMallocAsync((void**)&sm->s_in,
                            sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane), st)) !=
-          cudaSuccess)
+          cudaSuccess ||
+      (ctx->keep_exit &&
+       (e = cudaMallocAsync((void**)&sm->s_exit, sizeof(float2) * (size_t)(n_in * plane), st)) !=
+           cudaSuccess))
     return bail(cuda_fail(ctx, e, "S-matrix allocation"));
   if ((r = build_slices(ctx, spec, op, st, sm->t, sm->ptab)) != EELS_OK) return bail(r);
 
@@ -369,7 +379,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
       return bail(cuda_fail(ctx, e, "init plane waves"));
   }
   for (int i = 0; i < n_z; ++i) {
-    const bool last = (i == n_z - 1);
+    const bool last = (i == n_z - 1) && !sm->s_exit;   // the exit plane needs one more half step
     {
       Prof pr(ctx, "row_pass", st);
       e = launch_row_pass(n, n_in, W.p, Phi.p, sm->t + (int64_t)i * n * n, 0, 1,
@@ -383,6 +393,11 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "column pass"));
     }
   }
+  if (sm->s_exit) {   // psi_j(n_z) = F^-1 P F (t psi_j(n_z - 1)) is in W: store N Dec of it
+    Prof pr(ctx, "row_pass_store", st);
+    e = launch_row_pass(n, n_in, W.p, nullptr, sm->t, 0, 2, sm->s_exit, n_in, plane, 0, tw, st);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "exit plane store"));
+  }
   *out = sm;
   return EELS_OK;
 }
@@ -393,6 +408,7 @@ void eels_smatrix_free(eels_smatrix* sm) {
   cudaStreamSynchronize(sm->st);
   if (sm->t) cudaFreeAsync(sm->t, sm->st);
   if (sm->ptab) cudaFreeAsync(sm->ptab, sm->st);
+  if (sm->s_exit) cudaFreeAsync(sm->s_exit, sm->st);
   if (sm->s_in) cudaFreeAsync(sm->s_in, sm->st);
   delete sm;
 }
@@ -880,6 +896,130 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToHost, st));
     EELS_CK(cudaStreamSynchronize(st));
   }
+  return EELS_OK;
+}
+
+// First pixel of the L/f cut around r on one axis of the N/2 grid: the in-rule pixel
+// (same minimum-image rule as the site windows) whose cyclic predecessor is out of rule;
+// -1 if the in-rule pixels are not one cyclic run.  Every pixel in rule (f = 1): 0.
+static int cut_start(int nh, double cell, int f, double r) {
+  std::vector<char> ok(nh);
+  int count = 0;
+  for (int p = 0; p < nh; ++p) {
+    ok[p] = axis_in_window((double)p * (cell / nh), r, cell, f) ? 1 : 0;
+    count += ok[p];
+  }
+  if (count == nh) return 0;
+  int start = -1, runs = 0;
+  for (int p = 0; p < nh; ++p)
+    if (ok[p] && !ok[(p + nh - 1) % nh]) { start = p; ++runs; }
+  return runs == 1 ? start : -1;
+}
+
+eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eels_scan* sc,
+                                const eels_detector* det, int n_det, double* out,
+                                int out_on_device, void* stream) {
+  if (!ctx || !sm || !sc || !det || !out) return fail(ctx, EELS_ERR_ARG, "null argument");
+  if (!sm->s_exit)
+    return fail(ctx, EELS_ERR_ARG, "S-matrix built without the exit plane (EELS_OPT_EXIT_PLANE)");
+  if (n_det < 1 || n_det > eels::kMaxDetectors) return fail(ctx, EELS_ERR_ARG, "1..8 detectors");
+  if (sc->n_sx <= 0 || sc->n_sy <= 0) return fail(ctx, EELS_ERR_ARG, "empty scan");
+  const int n = sm->n, nh = n / 2, f = sm->f;
+  if (nh % f) return fail(ctx, EELS_ERR_UNSUPPORTED, "the L/f cut needs N/2 divisible by f");
+  const int m = nh / f;
+  if (!eels::cut_supported(m))
+    return fail(ctx, EELS_ERR_UNSUPPORTED, "cut size " + std::to_string(m) + " not built");
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].inner >= 0) || det[d].outer != det[d].outer)
+      return fail(ctx, EELS_ERR_ARG, "bad detector angles");
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n_in = (int)sm->bp.size();
+  const int64_t n_img = (int64_t)sc->n_sx * sc->n_sy;
+
+  // cut origins per scan column / row
+  std::vector<int> wx(sc->n_sx), wy(sc->n_sy);
+  for (int i = 0; i < sc->n_sx; ++i)
+    if ((wx[i] = cut_start(nh, sm->cell, f, sc->x0 + (double)i * sc->step_x)) < 0)
+      return fail(ctx, EELS_ERR_ARG, "probe cut is not one run of pixels");
+  for (int i = 0; i < sc->n_sy; ++i)
+    if ((wy[i] = cut_start(nh, sm->cell, f, sc->y0 + (double)i * sc->step_y)) < 0)
+      return fail(ctx, EELS_ERR_ARG, "probe cut is not one run of pixels");
+  // detector bins of the cut's DFT lattice k = f (a, b) / L, inside the band limit
+  std::vector<uint8_t> mask((size_t)m * m, 0);
+  for (int b = 0; b < m; ++b)
+    for (int a = 0; a < m; ++a) {
+      const int sa = a < (m + 1) / 2 ? a : a - m, sb = b < (m + 1) / 2 ? b : b - m;
+      const int64_t r2 = (int64_t)sa * sa + (int64_t)sb * sb;
+      if (16 * (int64_t)f * f * r2 >= (int64_t)n * n) continue;
+      const double k = f * std::sqrt((double)r2) / sm->cell;
+      for (int d = 0; d < n_det; ++d) {
+        bool in = sm->lam * k >= det[d].inner;
+        if (det[d].outer > 0) in = in && sm->lam * k <= det[d].outer;
+        if (in) mask[(size_t)b * m + a] |= (uint8_t)(1u << d);
+      }
+    }
+  float2* tw = nullptr;
+  eels_status r = twiddles(ctx, m, &tw);
+  if (r != EELS_OK) return r;
+  DevBuf<int> dwx, dwy, dbp, dbq;
+  DevBuf<uint8_t> dmask;
+  DevBuf<float2> ax, ay, cuts;
+  DevBuf<double> dimg;
+  EELS_CK(dwx.upload(wx.data(), wx.size(), st));
+  EELS_CK(dwy.upload(wy.data(), wy.size(), st));
+  EELS_CK(dmask.upload(mask.data(), mask.size(), st));
+  EELS_CK(dbp.upload(sm->bp.data(), n_in, st));
+  EELS_CK(dbq.upload(sm->bq.data(), n_in, st));
+  EELS_CK(ax.alloc((size_t)n_in * sc->n_sx, st));
+  EELS_CK(ay.alloc((size_t)n_in * sc->n_sy, st));
+  EELS_CK(eels::launch_phase_table(ax.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x, sc->n_sx, st));
+  EELS_CK(eels::launch_phase_table(ay.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y, sc->n_sy, st));
+  EELS_CK(dimg.alloc((size_t)n_det * n_img, st));
+  EELS_CK(cudaMemsetAsync(dimg.p, 0, sizeof(double) * n_det * n_img, st));
+  // scan rows in batches whose cuts fit in ~1 GiB
+  const int64_t per_row = (int64_t)sc->n_sx * m * m * (int64_t)sizeof(float2);
+  const int rows_b = (int)std::max<int64_t>(1, std::min<int64_t>(sc->n_sy, ((int64_t)1 << 30) / per_row));
+  EELS_CK(cuts.alloc((size_t)rows_b * sc->n_sx * m * m, st));
+  for (int iy0 = 0; iy0 < sc->n_sy; iy0 += rows_b) {
+    const int nr = std::min(rows_b, sc->n_sy - iy0);
+    {
+      Prof pr(ctx, "exit_cut", st);
+      EELS_CK(eels::launch_exit_cut(sm->s_exit, n_in, nh, m, ax.p, ay.p, sc->n_sx, sc->n_sy,
+                                    dwx.p, dwy.p, iy0, nr, cuts.p, st));
+    }
+    Prof pr(ctx, "cut_fft_detect", st);
+    EELS_CK(eels::launch_cut_detect(m, cuts.p, nr * sc->n_sx, dmask.p, n_det, sc->n_sx, iy0,
+                                    n_img, dimg.p, tw, st));
+  }
+  // I = (16 f^2 / N^2) (c^2 / N^2) sum |DFT|^2: S_exit carries N, the coefficients omit c
+  const double nn = (double)n * (double)n;
+  const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
+  EELS_CK(eels::launch_scale(dimg.p, n_det * n_img, scale, st));
+  if (out_on_device) {
+    EELS_CK(cudaMemcpyAsync(out, dimg.p, sizeof(double) * n_det * n_img, cudaMemcpyDeviceToDevice, st));
+  } else {
+    EELS_CK(cudaMemcpyAsync(out, dimg.p, sizeof(double) * n_det * n_img, cudaMemcpyDeviceToHost, st));
+    EELS_CK(cudaStreamSynchronize(st));
+  }
+  return EELS_OK;
+}
+
+eels_status eels_divide_map(eels_ctx* ctx, double* map, const double* bf, int n_types,
+                            int64_t n_pix, int on_device, void* stream) {
+  if (!ctx || !map || !bf || n_types < 0 || n_pix < 0) return fail(ctx, EELS_ERR_ARG, "bad arguments");
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (on_device) {
+    EELS_CK(eels::launch_divide(map, bf, n_types, n_pix, st));
+    return EELS_OK;
+  }
+  DevBuf<double> dm, db;
+  EELS_CK(dm.upload(map, (size_t)n_types * n_pix, st));
+  EELS_CK(db.upload(bf, (size_t)n_pix, st));
+  EELS_CK(eels::launch_divide(dm.p, db.p, n_types, n_pix, st));
+  EELS_CK(cudaMemcpyAsync(map, dm.p, sizeof(double) * n_types * n_pix, cudaMemcpyDeviceToHost, st));
+  EELS_CK(cudaStreamSynchronize(st));
   return EELS_OK;
 }
 

@@ -82,6 +82,22 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
                                double r0, double step, int n_pos, cudaStream_t s);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
 
+// Elastic images (elastic.cu).  Cut pass: out[r][sx][y'][x'] for scan rows iy0 ..
+// iy0 + n_rows - 1 = sum_j ax[j][sx] ay[j][iy] S[j][(wy[iy] + y') % nh][(wx[sx] + x') % nh].
+constexpr int kMaxDetectors = 8;
+bool cut_supported(int m);
+cudaError_t launch_exit_cut(const float2* S, int n_in, int nh, int m, const float2* ax,
+                            const float2* ay, int n_sx, int n_sy, const int* wx, const int* wy,
+                            int iy0, int n_rows, float2* out, cudaStream_t s);
+// map[m][p] /= bf[p] for m < n_types, p < n_pix.
+cudaError_t launch_divide(double* map, const double* bf, int n_types, int64_t n_pix,
+                          cudaStream_t s);
+// 2-D DFT of n_cut cuts of M x M (in place), then img[d][iy0 * n_sx + cut] += sum of
+// |X|^2 over the bins with bit d set in mask[ky][kx].
+cudaError_t launch_cut_detect(int m, float2* X, int n_cut, const uint8_t* mask, int n_det,
+                              int n_sx, int iy0, int64_t img_stride, double* img,
+                              const float2* tw, cudaStream_t s);
+
 // Tensor-core (tcgen05) contraction of a batch of sites of one slice: gathers the
 // windowed operands, runs GEMM 1 (M = Sout^H diag(H) Sin) and GEMM 2 with the fused
 // sum_d |.|^2 epilogue into map.  All pointers are device memory.  Operand buffers
