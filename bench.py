@@ -363,6 +363,12 @@ def gpu_arm(args, rank, world):
         quad = {"value": npos * wl.n_z / qs, "unit": UNIT, "probes": npos,
                 "multislice_ops": qsteps, "sample": f"{npos} seeded probes of the same scan"}
 
+    # elastic by-products (Sec. IV D) of the same S-matrix: ADF (60 mrad inner) and the
+    # incoherent bright field with the EELS aperture, plus the exit-plane cost of the build
+    elastic = None
+    if rank == 0 and not args.no_elastic:
+        elastic = elastic_run(g, ctx, wl, vdev, stream, args.precision)
+
     # roofline of the dominant kernel (CUDA-event times of every launch in the timed region).
     # Tensor peak: the measured burst figure when the sampled clocks show the GPU at its
     # maximum SM clock with no power cap during the timed region, else the sustained one
@@ -435,8 +441,55 @@ def gpu_arm(args, rank, world):
         "clocks": clk,
         "gpu_quadratic": quad,
         "accuracy": acc,
+        "elastic": elastic,
     }
     return line
+
+
+def elastic_run(g, ctx, wl, vdev, stream, precision, reps=3):
+    """Time the elastic images and the extra build work of the exit plane."""
+    import torch
+    dets = [(0.060, 0.0), (0.0, wl.beta)]
+    edge = wl.lam * wl.n / (4 * wl.cell)
+    if edge <= 0.060:
+        return {"skipped": f"band edge {edge * 1e3:.0f} mrad is below the 60 mrad ADF detector"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def build():
+        g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream).free()
+
+    t_build = timed(build)
+    ctx.set_exit_plane(True)
+    try:
+        t_build_exit = timed(build)
+        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
+        out = torch.zeros((2, wl.scan[1], wl.scan[0]), dtype=torch.float64, device="cuda")
+        ctx.profile_read()
+        ctx.profile_enable(True)
+        t_img = timed(lambda: ctx.elastic_images(sm, wl.scan, dets, out=out, stream=stream))
+        ctx.profile_enable(False)
+        prof = ctx.profile_read()
+        sm.free()
+    finally:
+        ctx.set_exit_plane(False)
+    img = out.cpu().numpy()
+    return {"detectors": {"adf": [0.060, None], "bf": [0.0, wl.beta]},
+            "images_ms": t_img, "probes_per_s": wl.n_scan / (t_img / 1e3),
+            "exit_plane_build_ms": t_build_exit - t_build, "build_ms": t_build,
+            "kernels": {k: {"launches": v["launches"] // (reps + 1),
+                            "ms": v["ms"] / (reps + 1)} for k, v in prof.items()},
+            "adf_mean": float(img[0].mean()), "bf_mean": float(img[1].mean())}
 
 
 def _window_count(s, r, cell, f):
@@ -590,6 +643,7 @@ def main():
                     help="how S_out reaches each depth (the paper's S_2 variants)")
     ap.add_argument("--s2-study", action="store_true",
                     help="print the S_out scheme thickness study instead of the bench line")
+    ap.add_argument("--no-elastic", action="store_true", help="skip the ADF / BF images")
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")

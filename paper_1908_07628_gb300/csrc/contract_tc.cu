@@ -60,8 +60,18 @@ struct Tile {
   static constexpr int A_BYTES = BM * P::BK * (int)sizeof(typename P::T);   // one plane
   static constexpr int B_BYTES = BN * P::BK * (int)sizeof(typename P::T);
   static constexpr int STAGE_BYTES = P::PLANES * (A_BYTES + B_BYTES);
-  static constexpr size_t SMEM = (size_t)P::STAGES * STAGE_BYTES + 1024 + 256;
 };
+
+// Pipeline depth of a GEMM mode.  TF32 runs two stages: two CTAs then share an SM
+// and one's epilogue overlaps the other's main loop.
+template <int MODE, int PREC>
+__host__ __device__ constexpr int stages_of() {
+  return PREC == EELS_TC_TF32 ? 2 : Prec<PREC>::STAGES;
+}
+template <int MODE, int PREC>
+__host__ __device__ constexpr size_t smem_of() {
+  return (size_t)stages_of<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + 1024 + 256;
+}
 
 // store the pair (a, b) at element e of a row, in every plane of the precision
 template <int PREC>
@@ -151,7 +161,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
   using P = Prec<PREC>;
   using TL = Tile<PREC>;
-  constexpr int STAGES = P::STAGES, BK = P::BK, PL = P::PLANES;
+  constexpr int STAGES = stages_of<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ float red[BN / 2];
   const int z = blockIdx.z;
@@ -241,20 +251,32 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       if (row < es.rows && col < es.cols) put16<PREC>(es.out, es.plane_stride, rbase + col, v);
     }
   } else if constexpr (MODE == 2) {
+    // Chunks of 32 columns (16 pixels): every thread forms its two output rows
+    // (H_t Y and -i H_t Y) for a group of channels in shared memory (the pipeline
+    // buffers, idle now), then the CTA writes whole 32-element row segments, so each
+    // warp store covers full 32-byte sectors instead of 32 scattered rows.
+    using T = typename P::T;
+    constexpr int CW = 32;                                   // columns per chunk
+    constexpr int RB = CW * (int)sizeof(T);                  // bytes of a row segment
+    constexpr int PITCH = RB + 16;                           // staging row pitch
+    constexpr int TILE = 2 * BM * PITCH;                     // one channel, one plane
+    constexpr int SEGS = RB / 16;                            // 16-byte parts of a segment
+    const int tg_max = (int)((size_t)STAGES * TL::STAGE_BYTES / ((size_t)PL * TILE));
     const int site = ey.slot_site[z];
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tc::tmem_ld16(trow + c, v);
-      const int col = n0 + c;   // 2 p
-      if (row < ey.rows && col < es.cols) {
-        for (int t = 0; t < ey.n_types; ++t) {
-          const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t) * ey.P;
-          const int64_t r0 = ((int64_t)z * ey.n_types + t) * ey.z_stride +
-                             (int64_t)(2 * row) * ey.row_pitch + col;
-          float hy[16], mhy[16];
+    const int rows_out = 2 * ey.rows;                        // rows of BV per channel
+    uint8_t* stg = sm;
+    for (int c = 0; c < BN && n0 + c < es.cols; c += CW) {
+      for (int t0 = 0; t0 < ey.n_types; t0 += tg_max) {
+        const int tg = min(tg_max, ey.n_types - t0);
+        float v[CW];
+        tc::tmem_ld16(trow + c, v);
+        tc::tmem_ld16(trow + c + 16, v + 16);
+        for (int tt = 0; tt < tg; ++tt) {
+          const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0 + tt) * ey.P;
+          float hy[CW], mhy[CW];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int pp = col / 2 + q;
+          for (int q = 0; q < CW / 2; ++q) {
+            const int pp = (n0 + c) / 2 + q;
             const float2 h = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
             const float2 y = cmul(h, make_float2(v[2 * q], v[2 * q + 1]));
             hy[2 * q] = y.x;
@@ -262,9 +284,55 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             mhy[2 * q] = y.y;
             mhy[2 * q + 1] = -y.x;
           }
-          put16<PREC>(ey.bv, ey.plane_stride, r0, hy);
-          put16<PREC>(ey.bv, ey.plane_stride, r0 + ey.row_pitch, mhy);
+          const int rr = 2 * (warp * 32 + lane);
+          uint8_t* d0 = stg + (size_t)(tt * PL) * TILE + (size_t)rr * PITCH;
+          if constexpr (PREC == EELS_TC_TF32) {
+            float4* a = reinterpret_cast<float4*>(d0);
+            float4* b = reinterpret_cast<float4*>(d0 + PITCH);
+#pragma unroll
+            for (int q = 0; q < CW / 4; ++q) {
+              a[q] = make_float4(tc::to_tf32(hy[4 * q]), tc::to_tf32(hy[4 * q + 1]),
+                                 tc::to_tf32(hy[4 * q + 2]), tc::to_tf32(hy[4 * q + 3]));
+              b[q] = make_float4(tc::to_tf32(mhy[4 * q]), tc::to_tf32(mhy[4 * q + 1]),
+                                 tc::to_tf32(mhy[4 * q + 2]), tc::to_tf32(mhy[4 * q + 3]));
+            }
+          } else {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              const float* src = half ? mhy : hy;
+              __align__(16) __nv_bfloat16 hi[CW], lo[CW];
+#pragma unroll
+              for (int q = 0; q < CW; ++q) {
+                hi[q] = __float2bfloat16_rn(src[q]);
+                lo[q] = __float2bfloat16_rn(src[q] - __bfloat162float(hi[q]));
+              }
+              uint4* dh = reinterpret_cast<uint4*>(d0 + half * PITCH);
+              uint4* dl = reinterpret_cast<uint4*>(d0 + TILE + half * PITCH);
+#pragma unroll
+              for (int q = 0; q < SEGS; ++q) {
+                dh[q] = reinterpret_cast<const uint4*>(hi)[q];
+                dl[q] = reinterpret_cast<const uint4*>(lo)[q];
+              }
+            }
+          }
         }
+        __syncthreads();
+        // coalesced copy-out: item = (channel, plane, row, 16-byte part)
+        const int items = tg * PL * 2 * BM * SEGS;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+          const int part = it % SEGS;
+          const int rr = (it / SEGS) % (2 * BM);
+          const int tp = it / (SEGS * 2 * BM);               // tt * PL + pl
+          const int tt = tp / PL, pl = tp % PL;
+          const int orow = 2 * m0 + rr;
+          if (orow >= rows_out) continue;
+          const int64_t e = ((int64_t)z * ey.n_types + t0 + tt) * ey.z_stride +
+                            (int64_t)pl * ey.plane_stride + (int64_t)orow * ey.row_pitch + n0 + c;
+          const uint4 val = *reinterpret_cast<const uint4*>(stg + (size_t)tp * TILE +
+                                                            (size_t)rr * PITCH + part * 16);
+          reinterpret_cast<uint4*>(static_cast<T*>(ey.bv) + e)[part] = val;
+        }
+        __syncthreads();
       }
     }
   } else {
@@ -493,13 +561,15 @@ template <int PREC>
 cudaError_t set_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
-  const int smem = (int)Tile<PREC>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0, PREC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_of<0, PREC>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tc_gemm<1, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_tc_gemm<1, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_of<1, PREC>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tc_gemm<2, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(k_tc_gemm<2, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_of<2, PREC>());
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -536,7 +606,7 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{};
   EpiSpread ey{};
   dim3 g1((b.k2p + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<0, PREC><<<g1, 128, Tile<PREC>::SMEM, st>>>(mA1, mB1, b.k1p / Prec<PREC>::BK,
+  k_tc_gemm<0, PREC><<<g1, 128, smem_of<0, PREC>(), st>>>(mA1, mB1, b.k1p / Prec<PREC>::BK,
                                                          b.a_batch1, b.b_batch1, b.n_valid1, nullptr,
                                                          es, ea, ey, b.status);
   return cudaGetLastError();
@@ -557,7 +627,7 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
              b.map, b.n_out};
   EpiSpread ey{};
   dim3 g2((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<1, PREC><<<g2, 128, Tile<PREC>::SMEM, st>>>(mM1, mB2, b.k2p / Prec<PREC>::BK,
+  k_tc_gemm<1, PREC><<<g2, 128, smem_of<1, PREC>(), st>>>(mM1, mB2, b.k2p / Prec<PREC>::BK,
                                                          b.a_batch2, b.b_batch2, b.n_valid2, nullptr,
                                                          es, ea, ey, b.status);
   return cudaGetLastError();
@@ -594,7 +664,7 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
                b.n_types, b.H, b.h_mul, b.slot_site};
   dim3 g((b.k1p + BN - 1) / BN, (b.nr_cap + BM - 1) / BM, b.n_sites);
-  k_tc_gemm<2, PREC><<<g, 128, Tile<PREC>::SMEM, st>>>(mAY, mBY, b.k2p / Prec<PREC>::BK,
+  k_tc_gemm<2, PREC><<<g, 128, smem_of<2, PREC>(), st>>>(mAY, mBY, b.k2p / Prec<PREC>::BK,
                                                         b.a_batch_y, b.a_batch_y, b.n_valid_y,
                                                         b.m_valid_y, es, ea, ey, b.status);
   return cudaGetLastError();
@@ -614,7 +684,7 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
              b.map, b.n_out};
   EpiSpread ey{};
   dim3 g((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<1, PREC><<<g, 128, Tile<PREC>::SMEM, st>>>(mA1, mBV, b.k1p / Prec<PREC>::BK,
+  k_tc_gemm<1, PREC><<<g, 128, smem_of<1, PREC>(), st>>>(mA1, mBV, b.k1p / Prec<PREC>::BK,
                                                         b.a_batch1, b.b_batch1, b.n_valid2, nullptr,
                                                         es, ea, ey, b.status);
   return cudaGetLastError();
