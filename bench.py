@@ -188,6 +188,61 @@ def _algorithmic(wl, n_in, n_out, prof):
     return out
 
 
+def crop_study(g, ctx, stream, widths=(64, 48, 30, 22, 15), reps=3):
+    """Sec. IV B trade-off: one dopant with a long-tailed transition potential in a
+    51.6 A rocksalt slab (2x2 cells, 128^2, f = 1, 32x32 scan over the cell); the
+    potential is cut to w x w pixels of the N/2 grid (0.134 A each; 64 = the whole cell).
+    Reports the contraction time (TF32, CUDA events of the gather and GEMM launches) and
+    the errors against the whole-cell map (FP32): total, and in the 1 A window around
+    the dopant (eps of the site pixels, and of their summed signal)."""
+    import torch
+    base = sp.dopant_slab(widths[0])
+    vdev = torch.from_numpy(base.vproj).cuda()
+    sm = g.build_smatrix_for(ctx, base, vproj=vdev, stream=stream)
+    rx, ry = base.scan_positions()
+    sx, sy = float(base.site_x[0]), float(base.site_y[0])
+    win = (np.abs(ry - sy)[:, None] <= 0.5) & (np.abs(rx - sx)[None, :] <= 0.5)
+    contraction = ("gemm", "tc_")
+
+    def contraction_ms(wl):
+        g.inelastic_map_for(ctx, sm, wl, "tf32", stream=stream)     # warm / tune
+        torch.cuda.synchronize()
+        ctx.profile_read()
+        ctx.profile_enable(True)
+        for _ in range(reps):
+            g.inelastic_map_for(ctx, sm, wl, "tf32", stream=stream)
+        ctx.profile_enable(False)
+        prof = ctx.profile_read()
+        return (sum(v["ms"] for k, v in prof.items() if k.startswith(contraction)) / reps,
+                sum(v["ms"] for v in prof.values()) / reps)
+
+    rows, ref = [], None
+    for w in widths:
+        wl = sp.dopant_slab(w)
+        fp = g.inelastic_map_for(ctx, sm, wl, "fp32", stream=stream)
+        t_c, t_all = contraction_ms(wl)
+        t_every, _ = contraction_ms(sp.dopant_slab(w, every_fe=True))
+        if ref is None:
+            ref = fp
+        d = fp - ref
+        rows.append({"w": w, "side_A": round(w * base.cell / (base.n // 2), 2),
+                     "contraction_ms": round(t_c, 3), "map_kernels_ms": round(t_all, 3),
+                     "contraction_ms_every_fe": round(t_every, 3),
+                     "eps_total": float(np.sqrt(np.sum(d ** 2) / np.sum(ref ** 2))),
+                     "eps_site": float(np.sqrt(np.sum(d[:, win] ** 2) / np.sum(ref[:, win] ** 2))),
+                     "site_signal_err": float(abs(fp[:, win].sum() - ref[:, win].sum())
+                                              / ref[:, win].sum())})
+    sm.free()
+    t0 = rows[0]["contraction_ms"]
+    t0e = rows[0]["contraction_ms_every_fe"]
+    for r in rows:
+        r["speedup_vs_whole_cell"] = round(t0 / r["contraction_ms"], 2)
+        r["speedup_vs_whole_cell_every_fe"] = round(t0e / r["contraction_ms_every_fe"], 2)
+    return {"workload": "dopant in rocksalt Fe-O 2x2x12 cells (51.6 A), 128^2, f=1, 32x32 scan",
+            "every_fe_sites": int(sp.dopant_slab(widths[0], every_fe=True).n_sites),
+            "site_pixels": int(win.sum()), "rows": rows}
+
+
 def s2_study(g, ctx, stream, thickness_cells=(5, 12, 19, 23), reps=2):
     """Sec. IV C trade-off on a rocksalt thickness series (8x8 cells, 256^2, f = 2, 16x16
     scan): map time of each S_out scheme (TF32 contraction) and the error of the
@@ -644,6 +699,8 @@ def main():
     ap.add_argument("--s2-study", action="store_true",
                     help="print the S_out scheme thickness study instead of the bench line")
     ap.add_argument("--no-elastic", action="store_true", help="skip the ADF / BF images")
+    ap.add_argument("--crop-study", action="store_true",
+                    help="print the crop-window study (Sec. IV B) instead of the bench line")
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")
@@ -683,6 +740,15 @@ def main():
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
                           "config": {"workload": "mixed map request stream (seed 4)"}}))
+        return
+    if args.crop_study:
+        import torch
+        from paper_1908_07628_gb300 import build
+        build.build()
+        import paper_1908_07628_gb300 as g
+        res = crop_study(g, g.Context(0), torch.cuda.current_stream())
+        print(json.dumps({"study": "crop window of the transition potential (Sec. IV B)",
+                          "data": "synthetic", **res}))
         return
     if args.s2_study:
         import torch

@@ -210,12 +210,13 @@ def projected_potentials(n: int, cell: float, n_z: int, x, y, sp, slice_idx) -> 
 
 
 def transition_windows(n: int, cell: float, w: int, site_x, site_y, m_list=(-1, 0, 1),
-                       amp: float = 0.01, r0: float = 0.3):
+                       amp: float = 0.01, r0: float = 0.3, tail: bool = False):
     """Synthetic L-edge-like transition potentials sampled on the N/2 grid.
 
-    H_m(r) = amp (r/r0)^|m| exp(-r^2/(2 r0^2)) exp(i m phi) about each site, on a
-    w x w window of the N/2 grid whose origin is (nearest pixel - w/2), taken
-    modulo N/2.  Returns (H complex64 [S][T][w][w], win_x0, win_y0).
+    H_m(r) = amp (r/r0)^|m| exp(-r^2/(2 r0^2)) exp(i m phi) about each site, or with
+    tail=True the long-tailed amp (r/r0)^|m| / (1 + (r/r0)^2)^((|m|+3)/2) exp(i m phi)
+    (decaying as r^-3), on a w x w window of the N/2 grid whose origin is (nearest
+    pixel - w/2), taken modulo N/2.  Returns (H complex64 [S][T][w][w], win_x0, win_y0).
     """
     nh = n // 2
     px = cell / nh
@@ -233,7 +234,11 @@ def transition_windows(n: int, cell: float, w: int, site_x, site_y, m_list=(-1, 
         r = np.hypot(DX, DY)
         phi = np.arctan2(DY, DX)
         for t, m in enumerate(m_list):
-            H[s, t] = amp * (r / r0) ** abs(m) * np.exp(-r * r / (2 * r0 * r0)) * np.exp(1j * m * phi)
+            if tail:
+                radial = (r / r0) ** abs(m) / (1.0 + (r / r0) ** 2) ** ((abs(m) + 3) / 2.0)
+            else:
+                radial = (r / r0) ** abs(m) * np.exp(-r * r / (2 * r0 * r0))
+            H[s, t] = amp * radial * np.exp(1j * m * phi)
         x0[s] = cx % nh
         y0[s] = cy % nh
     return H.astype(np.complex64), x0, y0
@@ -281,6 +286,38 @@ def rocksalt_slab(nzc: int, n: int = 256, ncell: int = 8, f: int = 2, scan_n: in
     scan_n^2 over the central cell: the thickness series of the S_2 scheme study."""
     return _crystal_workload(f"rocksalt_{ncell}x{ncell}x{nzc}_n{n}_f{f}", n=n, ncell=ncell,
                              nzc=nzc, f=f, w=32, scan_n=scan_n)
+
+
+def dopant_slab(w: int, n: int = 128, nzc: int = 12, scan_n: int = 32, r0: float = 0.4,
+                every_fe: bool = False):
+    """One dopant with a long-tailed transition potential in a rocksalt Fe-O slab.
+
+    2x2 cells (8.6 A) x nzc cells (2 nzc slices of a/2; 51.6 A for nzc = 12), n^2 grid,
+    f = 1.  The dopant replaces the Fe at the cell centre in the middle slice; its two
+    transitions (m = +2, -2) have the r^-3 tail of transition_windows(tail=True) and
+    are cut to a w x w window of the N/2 grid (w = n/2 is the whole cell).  The scan
+    covers the cell with scan_n^2 positions: the crop-window series of Sec. IV B.
+    every_fe=True puts the same transitions on every Fe of the slab (a contraction
+    large enough to time)."""
+    a = A_FEO
+    L = 2 * a
+    x, y, z, sp, lay = rocksalt_atoms(a, 2, 2, nzc)
+    n_z = 2 * nzc
+    vproj = projected_potentials(n, L, n_z, x, y, sp, lay)
+    mid = 2 * (nzc // 2)     # an even a/2 layer: it holds an Fe at (a, a)
+    if every_fe:
+        pick = np.nonzero(sp == "Fe")[0]
+    else:
+        pick = np.nonzero((sp == "Fe") & (lay == mid) & (np.abs(x - a) < 1e-9)
+                          & (np.abs(y - a) < 1e-9))[0]
+    sx, sy = x[pick].copy(), y[pick].copy()
+    H, wx, wy = transition_windows(n, L, w, sx, sy, m_list=(2, -2), r0=r0, tail=True)
+    scan = (scan_n, scan_n, 0.0, 0.0, L / scan_n, L / scan_n)
+    return Workload(name=f"dopant_2x2x{nzc}_n{n}_w{w}" + ("_allfe" if every_fe else ""), n=n,
+                    cell=L, n_z=n_z, dz=a / 2, lam=LAM_200KEV,
+                    sigma=interaction_constant(200e3, LAM_200KEV), f=1, alpha=0.020, beta=0.030,
+                    vproj=vproj, w=w, H=H, site_slice=lay[pick].astype(np.int32), site_x=sx,
+                    site_y=sy, win_x0=wx, win_y0=wy, scan=scan)
 
 
 def rocksalt_vacancy():

@@ -357,3 +357,28 @@ def test_inverse_scheme_is_exact_in_free_space(g, ctx):
     finally:
         ctx.set_sout_scheme("stream")
     assert exact.max() > 0 and eps(exact, got) < 1e-5
+
+
+# --- crop windows of a long-tailed transition potential (Sec. IV B) --------------------
+
+def test_crop_series_matches_oracle(g, ctx):
+    """The dopant slab (51.6 A) with its transition potential cut to 64 (the whole cell),
+    30 and 15 pixels of the N/2 grid: each map equals the oracle's, and the GPU crop
+    errors against the whole-cell map equal the oracle's."""
+    maps, refs = {}, {}
+    s_in = None
+    sm = None
+    for w in (64, 30, 15):
+        wl = sp.dopant_slab(w, scan_n=12)
+        if s_in is None:
+            s_in = lin.build_s_in(wl)
+            sm = g.build_smatrix_for(ctx, wl)
+        refs[w] = lin.linear_map(wl, s_in=s_in)
+        for prec in ("fp32", "tf32"):
+            got = g.inelastic_map_for(ctx, sm, wl, prec)
+            assert eps(refs[w], got) < EPS[prec], (w, prec)
+            maps[(w, prec)] = got
+    for w in (30, 15):
+        e_ref = eps(refs[64], refs[w])
+        e_gpu = eps(maps[(64, "fp32")], maps[(w, "fp32")])
+        assert e_ref > 1e-3 and abs(e_gpu - e_ref) < 1e-3 * e_ref + 1e-6, (w, e_ref, e_gpu)

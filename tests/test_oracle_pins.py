@@ -329,3 +329,28 @@ def test_window_rule_at_f1_admits_every_site_once():
     a = ms.axis_in_window(s, r, L, 2)
     b = ms.axis_in_window(s, r + L / 2, L, 2)
     assert np.all(a ^ b)
+
+
+# --- crop windows (Sec. IV B) -------------------------------------------------------
+
+def test_cropped_window_equals_full_window_zeroed_outside_the_crop():
+    """A w-pixel crop of the dopant's transition potential gives the map of the full
+    (whole-cell) window with H set to zero outside the same w x w pixels, and the crop
+    error falls as the crop grows (the long tail is cut less)."""
+    full = sp.dopant_slab(64, n=64, nzc=3, scan_n=6)
+    s_in = lin.build_s_in(full)
+    ref = lin.linear_map(full, s_in=s_in)
+    errs = []
+    for w in (8, 16, 24):
+        crop = sp.dopant_slab(w, n=64, nzc=3, scan_n=6)
+        got = lin.linear_map(crop, s_in=s_in)
+        # the same pixels inside the full window: offsets of the centred origins
+        off = (full.w // 2) - (w // 2)
+        zeroed = full.with_sites([0])
+        Hz = np.zeros_like(full.H)
+        Hz[:, :, off:off + w, off:off + w] = full.H[:, :, off:off + w, off:off + w]
+        zeroed.H = Hz
+        assert np.array_equal(Hz[:, :, off:off + w, off:off + w], crop.H)
+        assert ms.relative_error(lin.linear_map(zeroed, s_in=s_in), got) < 1e-12
+        errs.append(ms.relative_error(ref, got))
+    assert errs[0] > errs[1] > errs[2] > 0
