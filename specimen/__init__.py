@@ -281,6 +281,39 @@ def rocksalt_fp32():
                              scan_n=32)
 
 
+def rocksalt_phonons(k: int, u_rms: float = 0.08, seed: int = 5, ncell: int = 4, nzc: int = 6,
+                     n: int = 256, f: int = 2, scan_n: int = 16, w: int = 24):
+    """k frozen-phonon configurations of a rocksalt Fe-O crystal (ncell x ncell x nzc
+    cells, n^2 grid, f, scan_n^2 scan over the central cell).
+
+    Every atom is displaced in x and y by independent Gaussian offsets of standard
+    deviation u_rms (A), drawn from one seeded generator, configuration after
+    configuration (z, and so the slice of each atom, is kept).  Potentials and the
+    transition windows of the Fe sites follow the displaced atoms.  Returns a list of
+    Workloads with the same shapes."""
+    a = A_FEO
+    L = ncell * a
+    x0, y0, z, sp_, lay = rocksalt_atoms(a, ncell, ncell, nzc)
+    n_z = 2 * nzc
+    rng = np.random.default_rng(seed)
+    c0 = (ncell // 2) * a if ncell > 1 else 0.0
+    scan = (scan_n, scan_n, c0, c0, a / scan_n, a / scan_n)
+    out = []
+    for c in range(k):
+        x = (x0 + rng.normal(0.0, u_rms, x0.size)) % L
+        y = (y0 + rng.normal(0.0, u_rms, y0.size)) % L
+        vproj = projected_potentials(n, L, n_z, x, y, sp_, lay)
+        fe = sp_ == "Fe"
+        H, wx, wy = transition_windows(n, L, w, x[fe], y[fe])
+        out.append(Workload(name=f"rocksalt_{ncell}x{ncell}x{nzc}_n{n}_f{f}_fp{c}", n=n, cell=L,
+                            n_z=n_z, dz=a / 2, lam=LAM_200KEV,
+                            sigma=interaction_constant(200e3, LAM_200KEV), f=f, alpha=0.020,
+                            beta=0.030, vproj=vproj, w=w, H=H,
+                            site_slice=lay[fe].astype(np.int32), site_x=x[fe].copy(),
+                            site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=scan))
+    return out
+
+
 def rocksalt_slab(nzc: int, n: int = 256, ncell: int = 8, f: int = 2, scan_n: int = 16):
     """Rocksalt Fe-O ncell x ncell x nzc cells (2 nzc slices of a/2), n^2 grid, a scan of
     scan_n^2 over the central cell: the thickness series of the S_2 scheme study."""

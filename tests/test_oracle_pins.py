@@ -354,3 +354,29 @@ def test_cropped_window_equals_full_window_zeroed_outside_the_crop():
         assert ms.relative_error(lin.linear_map(zeroed, s_in=s_in), got) < 1e-12
         errs.append(ms.relative_error(ref, got))
     assert errs[0] > errs[1] > errs[2] > 0
+
+
+# --- frozen phonons ------------------------------------------------------------------
+
+def test_phonon_configurations_have_the_requested_displacements():
+    cfg = sp.rocksalt_phonons(4, u_rms=0.08, ncell=4, nzc=2, n=128, f=2, scan_n=4, w=16)
+    ref = sp.rocksalt_phonons(1, u_rms=0.0, ncell=4, nzc=2, n=128, f=2, scan_n=4, w=16)[0]
+    L = ref.cell
+    d = np.concatenate([((c.site_x - ref.site_x + L / 2) % L - L / 2) for c in cfg] +
+                       [((c.site_y - ref.site_y + L / 2) % L - L / 2) for c in cfg])
+    assert abs(d.mean()) < 4 * 0.08 / math.sqrt(d.size)
+    assert abs(d.std() / 0.08 - 1.0) < 4 / math.sqrt(2 * d.size)
+    assert all(np.array_equal(c.site_slice, ref.site_slice) for c in cfg)
+
+
+def test_phonon_average_is_the_mean_of_conventional_passes():
+    """The average over configurations equals the mean of the conventional (quadratic)
+    maps of the passes; with no displacement every pass is the static map."""
+    from oracle import phonon
+    cfg = sp.rocksalt_phonons(3, u_rms=0.1, ncell=2, nzc=2, n=64, f=1, scan_n=3, w=10)
+    avg = phonon.average_map(cfg)
+    quad = sum(ms.quadratic_map(c) for c in cfg) / len(cfg)
+    assert avg.max() > 0 and ms.relative_error(quad, avg) < 1e-12
+    assert ms.relative_error(lin.linear_map(cfg[0]), avg) > 1e-4     # the passes differ
+    still = sp.rocksalt_phonons(2, u_rms=0.0, ncell=2, nzc=2, n=64, f=1, scan_n=3, w=10)
+    assert ms.relative_error(ms.quadratic_map(still[0]), phonon.average_map(still)) < 1e-12
