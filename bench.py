@@ -243,6 +243,29 @@ def crop_study(g, ctx, stream, widths=(64, 48, 30, 22, 15), reps=3):
             "site_pixels": int(win.sum()), "rows": rows}
 
 
+def phonon_run(g, ctx, stream, k, precision, reps=2):
+    """Frozen-phonon average over k seeded configurations of the 512^2 rocksalt crystal
+    (8x8x20 cells, f = 2, 32x32 scan, u_rms = 0.08 A): pixel-slices/s counting every pass,
+    host inputs (the configurations' potentials and transition windows) copied inside
+    the timed region."""
+    import torch
+    cfg = sp.rocksalt_phonons(k, u_rms=0.08, ncell=8, nzc=20, n=512, f=2, scan_n=32, w=32)
+    out = torch.zeros((cfg[0].n_types, 32, 32), dtype=torch.float64, device="cuda")
+    ctx.phonon_map(cfg[:1], precision=precision, out=out, stream=stream)   # warm / tune
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.phonon_map(cfg, precision=precision, out=out, stream=stream)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    units = k * cfg[0].n_scan * cfg[0].n_z
+    static = cfg[0]
+    return {"configs": k, "u_rms_A": 0.08, "workload": "rocksalt Fe-O 8x8x20 cells, 512^2, f=2",
+            "value": units / dt, "unit": UNIT, "ms_per_pass": 1e3 * dt / k,
+            "precision": precision, "map_mean": float(out.mean().item()),
+            "h2d_bytes_per_pass": int(static.vproj.nbytes + static.H.nbytes)}
+
+
 def s2_study(g, ctx, stream, thickness_cells=(5, 12, 19, 23), reps=2):
     """Sec. IV C trade-off on a rocksalt thickness series (8x8 cells, 256^2, f = 2, 16x16
     scan): map time of each S_out scheme (TF32 contraction) and the error of the
@@ -699,6 +722,8 @@ def main():
     ap.add_argument("--s2-study", action="store_true",
                     help="print the S_out scheme thickness study instead of the bench line")
     ap.add_argument("--no-elastic", action="store_true", help="skip the ADF / BF images")
+    ap.add_argument("--phonons", type=int, default=0,
+                    help="print the frozen-phonon average over this many configurations")
     ap.add_argument("--crop-study", action="store_true",
                     help="print the crop-window study (Sec. IV B) instead of the bench line")
     ap.add_argument("--no-quadratic", action="store_true")
@@ -740,6 +765,16 @@ def main():
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
                           "config": {"workload": "mixed map request stream (seed 4)"}}))
+        return
+    if args.phonons:
+        import torch
+        from paper_1908_07628_gb300 import build
+        build.build()
+        import paper_1908_07628_gb300 as g
+        res = phonon_run(g, g.Context(0), torch.cuda.current_stream(), args.phonons,
+                         args.precision)
+        print(json.dumps({"study": "frozen-phonon average", "metric": METRIC, "data": "synthetic",
+                          **res}))
         return
     if args.crop_study:
         import torch

@@ -170,6 +170,19 @@ eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eel
                                 const eels_detector* detectors, int n_det, double* out,
                                 int out_on_device, void* stream);
 
+/* Frozen-phonon average of the EELS map: the mean over n_configs passes, each a full
+ * build + map of one configuration of thermally displaced atoms (specs[c], trs[c]; the
+ * displacements are the caller's), with the same optics, scan, beta and precision
+ * (Sec. IV A / IV D speak of frozen phonon passes).  Configurations must share the grid
+ * and the channel count (EELS_ERR_ARG otherwise); each may have its own sites.  The FP64
+ * sum runs on the device in configuration order, then is divided by n_configs.  Options
+ * of the context (grouping, S_out scheme, shards) apply to every pass.  map_out as for
+ * eels_inelastic_map. */
+eels_status eels_phonon_map(eels_ctx* ctx, const eels_specimen* specs,
+                            const eels_transitions* trs, int n_configs,
+                            const eels_optics* optics, const eels_scan* scan, double beta,
+                            int precision, double* map_out, int map_on_device, void* stream);
+
 /* The bright-field correction of Sec. IV D: map[m][p] /= bf[p] in place for every
  * channel m < n_types and pixel p < n_pix (FP64; both host or both device per
  * on_device; a zero bright-field pixel gives inf or nan there, as IEEE division does). */

@@ -87,6 +87,9 @@ EXPORTS = {
                                       C.c_void_p]),
     "eels_divide_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
                                   C.c_int, C.c_void_p]),
+    "eels_phonon_map": (C.c_int, [C.c_void_p, C.POINTER(Specimen), C.POINTER(Transitions),
+                                  C.c_int, C.POINTER(Optics), C.POINTER(Scan), C.c_double,
+                                  C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "eels_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
@@ -214,6 +217,35 @@ class Context:
         st = self._lib.eels_elastic_images(self._h, sm._h, C.byref(sc), dets, len(detectors), o,
                                            o_dev, _stream(stream))
         self._check(st, "eels_elastic_images")
+        if out is None or not o_dev:
+            if o_dev == 0 and out is not None and okeep is not out:
+                out[...] = okeep
+            return okeep if out is None else out
+        return out
+
+    def phonon_map(self, configs, precision="fp32", out=None, stream=None):
+        """eels_phonon_map over workload-like configurations (same grid, optics, scan,
+        beta and channels; each with its own vproj, H and sites): the mean map."""
+        c0 = configs[0]
+        specs = (Specimen * len(configs))()
+        trs = (Transitions * len(configs))()
+        keep = []
+        for i, wl in enumerate(configs):
+            v, v_dev, vk = _ptr(wl.vproj, np.float32)
+            specs[i] = Specimen(int(wl.n), int(wl.n_z), float(wl.cell), v, v_dev)
+            tr, tk = _transitions(wl.H, wl.site_slice, wl.win_x0, wl.win_y0, wl.site_x, wl.site_y)
+            trs[i] = tr
+            keep += [vk, tk]
+        op = Optics(float(c0.lam), float(c0.sigma), float(c0.dz), int(c0.f), float(c0.alpha))
+        sc = Scan(*[int(v) for v in c0.scan[:2]], *[float(v) for v in c0.scan[2:]])
+        shape = (int(c0.H.shape[-3]), int(c0.scan[1]), int(c0.scan[0]))
+        out_arr = np.zeros(shape) if out is None else out
+        o, o_dev, okeep = _ptr(out_arr, np.float64)
+        st = self._lib.eels_phonon_map(self._h, specs, trs, len(configs), C.byref(op), C.byref(sc),
+                                       float(c0.beta), EELS_PREC[precision], o, o_dev,
+                                       _stream(stream))
+        del keep
+        self._check(st, "eels_phonon_map")
         if out is None or not o_dev:
             if o_dev == 0 and out is not None and okeep is not out:
                 out[...] = okeep

@@ -1005,6 +1005,40 @@ eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eel
   return EELS_OK;
 }
 
+eels_status eels_phonon_map(eels_ctx* ctx, const eels_specimen* specs,
+                            const eels_transitions* trs, int n_configs, const eels_optics* optics,
+                            const eels_scan* sc, double beta, int precision, double* map_out,
+                            int map_on_device, void* stream) {
+  if (!ctx || !specs || !trs || !optics || !sc || !map_out || n_configs < 1)
+    return fail(ctx, EELS_ERR_ARG, "bad arguments");
+  for (int c = 1; c < n_configs; ++c)
+    if (specs[c].n != specs[0].n || trs[c].n_types != trs[0].n_types)
+      return fail(ctx, EELS_ERR_ARG, "configurations differ in grid or channel count");
+  EELS_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n_map = (int64_t)trs[0].n_types * sc->n_sx * sc->n_sy;
+  DevBuf<double> acc, one;
+  EELS_CK(acc.alloc((size_t)n_map, st));
+  EELS_CK(one.alloc((size_t)n_map, st));
+  EELS_CK(cudaMemsetAsync(acc.p, 0, sizeof(double) * n_map, st));
+  for (int c = 0; c < n_configs; ++c) {
+    eels_smatrix* sm = nullptr;
+    eels_status r = eels_build_smatrix(ctx, &specs[c], optics, stream, &sm);
+    if (r == EELS_OK) r = eels_inelastic_map(ctx, sm, &trs[c], sc, beta, precision, one.p, 1, stream);
+    eels_smatrix_free(sm);
+    if (r != EELS_OK) return r;
+    EELS_CK(eels::launch_accumulate(acc.p, one.p, n_map, st));
+  }
+  EELS_CK(eels::launch_scale(acc.p, n_map, 1.0 / n_configs, st));
+  if (map_on_device) {
+    EELS_CK(cudaMemcpyAsync(map_out, acc.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
+  } else {
+    EELS_CK(cudaMemcpyAsync(map_out, acc.p, sizeof(double) * n_map, cudaMemcpyDeviceToHost, st));
+    EELS_CK(cudaStreamSynchronize(st));
+  }
+  return EELS_OK;
+}
+
 eels_status eels_divide_map(eels_ctx* ctx, double* map, const double* bf, int n_types,
                             int64_t n_pix, int on_device, void* stream) {
   if (!ctx || !map || !bf || n_types < 0 || n_pix < 0) return fail(ctx, EELS_ERR_ARG, "bad arguments");

@@ -211,6 +211,13 @@ __global__ void k_phase_table(float2* __restrict__ out, const int* __restrict__ 
   }
 }
 
+__global__ void k_accumulate(double* __restrict__ acc, const double* __restrict__ x,
+                             int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] += x[i];
+}
+
 __global__ void k_scale(double* a, int64_t count, double scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -246,6 +253,12 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
   const int total = n_beams * n_pos;
   if (total <= 0) return cudaSuccess;
   k_phase_table<<<(total + 255) / 256, 256, 0, s>>>(out, bidx, n_beams, f, cell, r0, step, n_pos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_accumulate<<<256, 256, 0, s>>>(acc, x, count);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,8 @@ cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out,
 cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
                                double r0, double step, int n_pos, cudaStream_t s);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
+// acc[i] += x[i]
+cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s);
 
 // Elastic images (elastic.cu).  Cut pass: out[r][sx][y'][x'] for scan rows iy0 ..
 // iy0 + n_rows - 1 = sum_j ax[j][sx] ay[j][iy] S[j][(wy[iy] + y') % nh][(wx[sx] + x') % nh].

@@ -382,3 +382,21 @@ def test_crop_series_matches_oracle(g, ctx):
         e_ref = eps(refs[64], refs[w])
         e_gpu = eps(maps[(64, "fp32")], maps[(w, "fp32")])
         assert e_ref > 1e-3 and abs(e_gpu - e_ref) < 1e-3 * e_ref + 1e-6, (w, e_ref, e_gpu)
+
+
+# --- frozen phonons -----------------------------------------------------------------------
+
+def test_phonon_average_matches_oracle(g, ctx):
+    from oracle import phonon
+    cfg = sp.rocksalt_phonons(3, u_rms=0.1, ncell=2, nzc=3, n=128, f=2, scan_n=4, w=16)
+    ref = phonon.average_map(cfg)
+    assert ref.max() > 0
+    for prec in ("fp32", "tf32", "bf16x3"):
+        got = ctx.phonon_map(cfg, precision=prec)
+        assert eps(ref, got) < EPS[prec], prec
+    one = ctx.phonon_map(cfg[:1])
+    assert eps(g.inelastic_map_for(ctx, g.build_smatrix_for(ctx, cfg[0]), cfg[0], "fp32"), one) < 1e-12
+    with pytest.raises(g.EelsError) as e:
+        ctx.phonon_map([cfg[0], sp.rocksalt_phonons(1, ncell=2, nzc=3, n=256, f=2, scan_n=4,
+                                                     w=16)[0]])
+    assert e.value.status == 1
