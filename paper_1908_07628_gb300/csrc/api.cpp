@@ -562,6 +562,15 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   EELS_CK(ay.alloc((size_t)n_in * sc->n_sy, st));
   EELS_CK(eels::launch_phase_table(ax.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x, sc->n_sx, st));
   EELS_CK(eels::launch_phase_table(ay.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y, sc->n_sy, st));
+  DevBuf<float2> axT, ayT;   // [pos][n_in]: the tensor-core gathers read along the beams
+  if (tc) {
+    EELS_CK(axT.alloc((size_t)n_in * sc->n_sx, st));
+    EELS_CK(ayT.alloc((size_t)n_in * sc->n_sy, st));
+    EELS_CK(eels::launch_phase_table(axT.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x,
+                                     sc->n_sx, st, 1));
+    EELS_CK(eels::launch_phase_table(ayT.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y,
+                                     sc->n_sy, st, 1));
+  }
 
   // flattened transition lists of all slices
   std::vector<int> all_site, all_type, slice_off(n_z + 1, 0);
@@ -699,6 +708,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.z_type = dzt.p + (int64_t)q0 * T; b.n_sites = ns; b.slots_cap = sb;
       b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
       b.ax = ax.p; b.ay = ay.p; b.n_sx = sc->n_sx; b.n_sy = sc->n_sy;
+      b.axT = axT.p; b.ayT = ayT.p;
       b.xoff = dxoff.p; b.xcnt = dxcnt.p; b.xlist = dxlist.p;
       b.yoff = dyoff.p; b.ycnt = dycnt.p; b.ylist = dylist.p; b.nr_cap = nr_cap;
       b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;

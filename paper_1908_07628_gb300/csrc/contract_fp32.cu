@@ -198,10 +198,12 @@ k_gemm2_abs2(const float2* __restrict__ M, int64_t m_stride, int n_out, int n_in
 }
 
 __global__ void k_phase_table(float2* __restrict__ out, const int* __restrict__ bidx, int n_beams,
-                              int f, double cell, double r0, double step, int n_pos) {
+                              int f, double cell, double r0, double step, int n_pos,
+                              int transposed) {
   const int total = n_beams * n_pos;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int j = i / n_pos, r = i % n_pos;
+    const int j = transposed ? i % n_beams : i / n_pos;
+    const int r = transposed ? i / n_beams : i % n_pos;
     const double R = __dadd_rn(r0, __dmul_rn((double)r, step));
     double cyc = (double)f * (double)bidx[j] * R / cell;   // exp(-2 pi i cyc)
     cyc -= floor(cyc);
@@ -249,10 +251,11 @@ cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out,
 }
 
 cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
-                               double r0, double step, int n_pos, cudaStream_t s) {
+                               double r0, double step, int n_pos, cudaStream_t s, int transposed) {
   const int total = n_beams * n_pos;
   if (total <= 0) return cudaSuccess;
-  k_phase_table<<<(total + 255) / 256, 256, 0, s>>>(out, bidx, n_beams, f, cell, r0, step, n_pos);
+  k_phase_table<<<(total + 255) / 256, 256, 0, s>>>(out, bidx, n_beams, f, cell, r0, step, n_pos,
+                                                    transposed);
   return cudaGetLastError();
 }
 

@@ -438,8 +438,8 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
 // B2[slot][plane][2r] = conj(a_r), B2[slot][plane][2r+1] = i conj(a_r),
 // a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
 template <int PREC>
-__global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __restrict__ ay,
-                               int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
+__global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __restrict__ ayT,
+                               int n_in, const int* __restrict__ slot_site,
                                const int* __restrict__ xoff, const int* __restrict__ xcnt,
                                const int* __restrict__ xlist, const int* __restrict__ yoff,
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
@@ -448,6 +448,7 @@ __global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __re
   const int r = blockIdx.x, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
+  if (2 * r >= (2 * nr + BN - 1) / BN * BN) return;   // rows of N tiles GEMM 2 skips
   const int64_t pstride = (int64_t)2 * nr_cap * k2p;
   const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)(2 * r) * k2p;
   const int64_t r1 = r0 + k2p;
@@ -456,18 +457,20 @@ __global__ void k_gather_probe(const float2* __restrict__ ax, const float2* __re
     ix = xlist[xoff[s] + r % nx];
     iy = ylist[yoff[s] + r / nx];
   }
+  const float2* axr = axT + (int64_t)ix * n_in;
+  const float2* ayr = ayT + (int64_t)iy * n_in;
   for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
     float2 a = make_float2(0.f, 0.f);
-    if (r < nr && j < n_in) a = cmul(ax[(int64_t)j * n_sx + ix], ay[(int64_t)j * n_sy + iy]);
+    if (r < nr && j < n_in) a = cmul(axr[j], ayr[j]);
     put2<PREC>(B2, pstride, r0 + 2 * j, a.x, -a.y);
     put2<PREC>(B2, pstride, r1 + 2 * j, a.y, a.x);
   }
 }
 
-// AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
+// AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = axT[ix(r)][j] ayT[iy(r)][j]
 template <int PREC>
-__global__ void k_gather_arows(const float2* __restrict__ ax, const float2* __restrict__ ay,
-                               int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
+__global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __restrict__ ayT,
+                               int n_in, const int* __restrict__ slot_site,
                                const int* __restrict__ xoff, const int* __restrict__ xcnt,
                                const int* __restrict__ xlist, const int* __restrict__ yoff,
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
@@ -476,6 +479,7 @@ __global__ void k_gather_arows(const float2* __restrict__ ax, const float2* __re
   const int r = blockIdx.x, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
+  if (r >= (nr + BM - 1) / BM * BM) return;   // rows of M tiles GEMM-Y skips
   const int64_t pstride = (int64_t)nr_cap * k2p;
   const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)r * k2p;
   int ix = 0, iy = 0;
@@ -483,9 +487,11 @@ __global__ void k_gather_arows(const float2* __restrict__ ax, const float2* __re
     ix = xlist[xoff[s] + r % nx];
     iy = ylist[yoff[s] + r / nx];
   }
+  const float2* axr = axT + (int64_t)ix * n_in;
+  const float2* ayr = ayT + (int64_t)iy * n_in;
   for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
     float2 a = make_float2(0.f, 0.f);
-    if (r < nr && j < n_in) a = cmul(ax[(int64_t)j * n_sx + ix], ay[(int64_t)j * n_sy + iy]);
+    if (r < nr && j < n_in) a = cmul(axr[j], ayr[j]);
     put2<PREC>(AY, pstride, r0 + 2 * j, a.x, a.y);
   }
 }
@@ -587,8 +593,8 @@ cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
                                                           b.wy, b.B1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_probe<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
-      b.ax, b.ay, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt,
-      b.ylist, b.nr_cap, b.B2, b.k2p);
+      b.axT, b.ayT, b.n_in, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
+      b.nr_cap, b.B2, b.k2p);
   return cudaGetLastError();
 }
 
@@ -642,8 +648,8 @@ cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
                                                                  b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_arows<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
-      b.ax, b.ay, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt,
-      b.ylist, b.nr_cap, b.AY, b.k2p);
+      b.axT, b.ayT, b.n_in, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
+      b.nr_cap, b.AY, b.k2p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   dim3 gt((b.k1p / 2 + 31) / 32, (b.k2p / 2 + 31) / 32, b.n_sites);
   k_gather_sin_t<PREC><<<gt, 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.slot_site, b.wx, b.wy,

@@ -78,8 +78,10 @@ cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out,
                                    const TransitionBatch& tb, const WindowLists& wl, double* map,
                                    cudaStream_t s);
 // ax[j][ix] = exp(-2 pi i f p_j Rx(ix) / L) (FP64 phase); same for ay with q_j, Ry.
+// transposed = 1 writes out[pos][j] instead (coalesced reads along the beams).
 cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
-                               double r0, double step, int n_pos, cudaStream_t s);
+                               double r0, double step, int n_pos, cudaStream_t s,
+                               int transposed = 0);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
 // acc[i] += x[i]
 cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s);
@@ -131,6 +133,7 @@ struct TcBatch {
   void* AY; void* BY; void* BV;           // a rows, S_in window transposed, H_t . Y rows
   const int* a_batch_y; const int* n_valid_y;   // identity map and k1p per site
   const int* m_valid_y;                         // scan positions of the site of each slot
+  const float2* axT; const float2* ayT;         // phase tables [pos][n_in] (transposed)
 };
 cudaError_t tc_gather(const TcBatch& b, cudaStream_t s);   // A1, B1, B2 operand buffers
 cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t s);    // M1 = GEMM 1
