@@ -645,6 +645,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus, daby, dnvy, dnry;
   DevBuf<double> dscratch;
   std::vector<int> slot_all, zs_all, zt_all, nv2_all, nr_all, site_off(n_z + 1, 0);
+  std::vector<int> pv_all, py_all;
+  DevBuf<int> dtile_v, dtile_y;
   if (tc) {
     for (int i = 0; i < n_z; ++i) {
       site_off[i] = (int)slot_all.size();
@@ -659,12 +661,24 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       }
     }
     site_off[n_z] = (int)slot_all.size();
+    // prefix sums of the tiles with work, over all transitions (GEMM 2 / GEMM-V: column
+    // tiles of 2 n_R x every row tile of n_out) and over all sites (GEMM-Y: row tiles of
+    // n_R x every column tile of 2 w^2); a batch reads its slice of them
+    const int64_t gy_v = (n_out + 127) / 128, gx_y = (k1p + 255) / 256;
+    pv_all.assign(nv2_all.size() + 1, 0);
+    for (size_t z = 0; z < nv2_all.size(); ++z)
+      pv_all[z + 1] = pv_all[z] + (int)(((int64_t)nv2_all[z] + 255) / 256 * gy_v);
+    py_all.assign(nr_all.size() + 1, 0);
+    for (size_t q = 0; q < nr_all.size(); ++q)
+      py_all[q + 1] = py_all[q] + (int)(((int64_t)nr_all[q] + 127) / 128 * gx_y);
     std::vector<int> ab1(sb * T), bb1(sb * T), nv1(sb * T, k2p), ab2(sb * T), bb2(sb * T);
     for (int z = 0; z < sb * T; ++z) { ab1[z] = z / T; bb1[z] = z; ab2[z] = z; bb2[z] = z / T; }
     EELS_CK(dslot.upload(slot_all.data(), slot_all.size(), st));
     EELS_CK(dzs.upload(zs_all.data(), zs_all.size(), st));
     EELS_CK(dzt.upload(zt_all.data(), zt_all.size(), st));
     EELS_CK(dnv2.upload(nv2_all.data(), nv2_all.size(), st));
+    EELS_CK(dtile_v.upload(pv_all.data(), pv_all.size(), st));
+    EELS_CK(dtile_y.upload(py_all.data(), py_all.size(), st));
     EELS_CK(dab1.upload(ab1.data(), ab1.size(), st));
     EELS_CK(dbb1.upload(bb1.data(), bb1.size(), st));
     EELS_CK(dnv1.upload(nv1.data(), nv1.size(), st));
@@ -709,6 +723,10 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
       b.ax = ax.p; b.ay = ay.p; b.n_sx = sc->n_sx; b.n_sy = sc->n_sy;
       b.axT = axT.p; b.ayT = ayT.p;
+      b.tiles_v = dtile_v.p + (int64_t)q0 * T;
+      b.n_tiles_v = pv_all[(size_t)(q0 + ns) * T] - pv_all[(size_t)q0 * T];
+      b.tiles_y = dtile_y.p + q0;
+      b.n_tiles_y = py_all[q0 + ns] - py_all[q0];
       b.xoff = dxoff.p; b.xcnt = dxcnt.p; b.xlist = dxlist.p;
       b.yoff = dyoff.p; b.ycnt = dycnt.p; b.ylist = dylist.p; b.nr_cap = nr_cap;
       b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;

@@ -17,14 +17,18 @@
 //           planes); each product is lo*hi + hi*lo + hi*hi with kind::f16 MMAs into
 //           the same FP32 accumulator (the lo*lo term is below FP32 resolution).
 // Operands are gathered into K-padded buffers [batch][plane][rows][K] and streamed
-// by TMA (128-byte swizzle) through an mbarrier pipeline.  One 128 x 256 tile per
-// CTA: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMA, all four warps drain
-// TMEM in the epilogue.
+// by TMA (128-byte swizzle) through an mbarrier pipeline.  TF32 runs a persistent,
+// warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws);
+// BF16 hi + lo runs one 128 x 256 tile per CTA (k_tc_gemm): warp 0 lane 0 issues TMA,
+// warp 1 lane 0 issues MMA, all four warps drain TMEM in the epilogue.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "internal.h"
+
 #include "tc_ptx.cuh"
 
 namespace eels {
@@ -384,6 +388,295 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (!ok && status) atomicExch(status, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised TF32 form of the same three GEMMs.  One CTA per SM walks
+// the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 issues the TMA loads, warp 1
+// the MMAs, warps 2-9 run the epilogue (two per TMEM lane quarter, each pair splitting
+// the 256 columns).  The accumulator is double-buffered in TMEM (2 x 256 columns), so
+// the MMAs of the next tile overlap the epilogue of this one.  Every wait is bounded; a
+// failed wait stops every role (the four epilogue warps of a column half decide together
+// after their named barrier), and before returning the CTA waits, again bounded, for its
+// MMAs and its loads in flight, then frees its TMEM.
+// ---------------------------------------------------------------------------
+namespace ws {
+constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter, one per column half
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int CW = 32;                          // GEMM-Y epilogue chunk (columns)
+constexpr int PITCH = CW * 4 + 16;              // staging row pitch (bytes)
+constexpr int TILE = 2 * BM * PITCH;            // one channel of a chunk
+constexpr int TG = 1;                           // channels staged at once per column half
+template <int MODE>
+__host__ __device__ constexpr int stages() { return MODE == 2 ? 3 : 4; }
+template <int MODE>
+__host__ __device__ constexpr size_t staging() { return MODE == 2 ? (size_t)2 * TG * TILE : 0; }
+template <int MODE>
+__host__ __device__ constexpr size_t smem() {
+  return (size_t)stages<MODE>() * Tile<EELS_TC_TF32>::STAGE_BYTES + staging<MODE>() + 1024 + 256;
+}
+}  // namespace ws
+
+// named barrier of the four epilogue warps of one column half (ids 1 and 2)
+__device__ __forceinline__ void epi_sync(int half) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(ws::THREADS, 1)
+k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+             int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
+             const int* __restrict__ a_batch, const int* __restrict__ b_batch,
+             const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
+             EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
+  using P = Prec<EELS_TC_TF32>;
+  using TL = Tile<EELS_TC_TF32>;
+  constexpr int S = ws::stages<MODE>(), BK = P::BK;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ float red[BN / 2];
+  __shared__ int abort_flag;
+  const uint32_t raw = tc::smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* stg = sm + S * TL::STAGE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + ws::staging<MODE>());
+  uint64_t* empty = full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(full + s, 1);
+      tc::mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(acc_full + b, 1);
+      tc::mbar_init(acc_empty + b, ws::EPI_WARPS);   // one arrival per epilogue warp
+    }
+    tc::mbar_init(drain, 1);
+    abort_flag = 0;
+    tc::fence_barrier_init();
+    tc::tma_prefetch(&ta);
+    tc::tma_prefetch(&tb);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_holder, 2 * BN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  bool ok = true;
+
+  // Work list.  With tile_prefix, problem z owns the tiles tile_prefix[z] - tile_prefix[0]
+  // .. tile_prefix[z + 1] - tile_prefix[0] (exclusive), a rectangle of nx column tiles
+  // (column tile fastest) by its row tiles; only tiles with work are listed, so the
+  // round-robin below gives every CTA the same amount of work.  Without it every tile
+  // of the gx x gy x gz grid is listed.
+  const int base = tile_prefix ? tile_prefix[0] : 0;
+  const int tiles = tile_prefix ? tile_prefix[gz] - base : gx * gy * gz;
+  auto decode = [&](int t, int& z, int& n0, int& m0) {
+    if (!tile_prefix) {
+      z = t / (gx * gy);
+      m0 = ((t / gx) % gy) * BM;
+      n0 = (t % gx) * BN;
+    } else {
+      int lo = 0, hi = gz - 1;            // last z with tile_prefix[z] - base <= t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_prefix[mid] - base <= t) lo = mid; else hi = mid - 1;
+      }
+      z = lo;
+      const int local = t - (tile_prefix[z] - base);
+      const int count = tile_prefix[z + 1] - tile_prefix[z];
+      const int nx = MODE == 2 ? gx : count / gy;
+      n0 = (local % nx) * BN;
+      m0 = (local / nx) * BM;
+    }
+    return !(n0 >= n_valid[z] || (m_valid && m0 >= m_valid[z]));
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        int z, n0, m0;
+        if (!decode(t, z, n0, m0)) continue;
+        const int ab = a_batch[z], bb = b_batch[z];
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % S;
+          if (it >= S && !(ok = tc::mbar_wait(empty + s, ((it / S) - 1) & 1))) break;
+          uint8_t* st = sm + s * TL::STAGE_BYTES;
+          tc::mbar_arrive_expect_tx(full + s, TL::STAGE_BYTES);
+          tc::tma_load_4d(st, &ta, full + s, kb * BK, m0, 0, ab);
+          tc::tma_load_4d(st + TL::A_BYTES, &tb, full + s, kb * BK, n0, 0, bb);
+        }
+      }
+      // the last load of every stage has landed before the CTA may leave
+      for (int j = max(0, it - S); j < it; ++j) ok &= tc::mbar_wait(full + j % S, (j / S) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, i = 0;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        int z, n0, m0;
+        if (!decode(t, z, n0, m0)) continue;
+        const int b = i & 1;
+        if (i >= 2 && !(ok = tc::mbar_wait(acc_empty + b, ((i >> 1) - 1) & 1))) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+        for (int kb = 0; kb < kblocks; ++kb, ++it) {
+          const int s = it % S;
+          if (!(ok = tc::mbar_wait(full + s, (it / S) & 1))) break;
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(sm + s * TL::STAGE_BYTES);
+          const uint32_t sb = sa + TL::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_tf32(d, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32), P::IDESC,
+                         (kb | kk) != 0 ? 1u : 0u);
+          tc::mma_commit(empty + s);
+        }
+        if (!ok) break;
+        tc::mma_commit(acc_full + b);
+        ++i;
+      }
+      // every MMA issued has completed before the TMEM is freed
+      tc::mma_commit(drain);
+      ok &= tc::mbar_wait(drain, 0);
+    }
+  } else {
+    const int q4 = warp & 3;                  // TMEM lane quarter this warp may read
+    const int half = (warp - 2) >> 2;         // column half of the tile
+    const int te = threadIdx.x - 64 - 128 * half;   // 0 .. 127 within the half
+    const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
+    uint8_t* stg_h = stg + (size_t)half * ws::TG * ws::TILE;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      int z, n0, m0;
+      if (!decode(t, z, n0, m0)) continue;
+      const int b = i & 1;
+      if (!tc::mbar_wait(acc_full + b, (i >> 1) & 1)) atomicOr(&abort_flag, 1);
+      epi_sync(half);
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t trow = tmem + (uint32_t)(b * BN) + ((uint32_t)(q4 * 32) << 16);
+      const int row = m0 + q4 * 32 + lane;
+      if constexpr (MODE == 0) {
+        const int64_t rbase = (int64_t)z * es.z_stride + (int64_t)row * es.row_pitch;
+        for (int c = c_lo; c < c_hi; c += 16) {
+          float v[16];
+          tc::tmem_ld16(trow + c, v);
+          const int col = n0 + c;
+          if (row < es.rows && col < es.cols)
+            put16<EELS_TC_TF32>(es.out, es.plane_stride, rbase + col, v);
+        }
+      } else if constexpr (MODE == 2) {
+        const int site = ey.slot_site[z];
+        const int rows_out = 2 * ey.rows;
+        constexpr int SEGS = ws::CW * 4 / 16;
+        for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += ws::CW) {
+          for (int t0 = 0; t0 < ey.n_types; t0 += ws::TG) {
+            const int tg = min(ws::TG, ey.n_types - t0);
+            float v[ws::CW];
+            tc::tmem_ld16(trow + c, v);
+            tc::tmem_ld16(trow + c + 16, v + 16);
+            for (int tt = 0; tt < tg; ++tt) {
+              const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0 + tt) * ey.P;
+              uint8_t* d0 = stg_h + (size_t)tt * ws::TILE + (size_t)(2 * (q4 * 32 + lane)) * ws::PITCH;
+              float4* a = reinterpret_cast<float4*>(d0);
+              float4* bq = reinterpret_cast<float4*>(d0 + ws::PITCH);
+#pragma unroll
+              for (int q = 0; q < ws::CW / 4; ++q) {
+                const int pp = (n0 + c) / 2 + 2 * q;
+                const float2 h0 = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
+                const float2 h1 = pp + 1 < ey.P ? __ldg(Ht + pp + 1) : make_float2(0.f, 0.f);
+                const float2 y0 = cmul(h0, make_float2(v[4 * q], v[4 * q + 1]));
+                const float2 y1 = cmul(h1, make_float2(v[4 * q + 2], v[4 * q + 3]));
+                a[q] = make_float4(tc::to_tf32(y0.x), tc::to_tf32(y0.y), tc::to_tf32(y1.x),
+                                   tc::to_tf32(y1.y));
+                bq[q] = make_float4(tc::to_tf32(y0.y), tc::to_tf32(-y0.x), tc::to_tf32(y1.y),
+                                    tc::to_tf32(-y1.x));
+              }
+            }
+            epi_sync(half);
+            const int items = tg * 2 * BM * SEGS;
+            for (int it2 = te; it2 < items; it2 += 128) {
+              const int part = it2 % SEGS;
+              const int rr = (it2 / SEGS) % (2 * BM);
+              const int tt = it2 / (SEGS * 2 * BM);
+              const int orow = 2 * m0 + rr;
+              if (orow >= rows_out) continue;
+              const int64_t e = ((int64_t)z * ey.n_types + t0 + tt) * ey.z_stride +
+                                (int64_t)orow * ey.row_pitch + n0 + c;
+              const uint4 val = *reinterpret_cast<const uint4*>(stg_h + (size_t)tt * ws::TILE +
+                                                                (size_t)rr * ws::PITCH + part * 16);
+              reinterpret_cast<uint4*>(static_cast<float*>(ey.bv) + e)[part] = val;
+            }
+            epi_sync(half);
+          }
+        }
+      } else {
+        // this half owns red[c_lo / 2 .. c_hi / 2)
+        for (int k = c_lo / 2 + te; k < c_hi / 2; k += 128) red[k] = 0.f;
+        epi_sync(half);
+        const bool live = row < ea.rows;
+        for (int c = c_lo; c < c_hi; c += 16) {
+          float v[16];
+          tc::tmem_ld16(trow + c, v);
+          float p[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            p[q] = live ? fmaf(v[2 * q], v[2 * q], v[2 * q + 1] * v[2 * q + 1]) : 0.f;
+          const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+          float r4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float send = b4 ? p[q] : p[q + 4];
+            r4[q] = (b4 ? p[q + 4] : p[q]) + __shfl_xor_sync(0xffffffffu, send, 16);
+          }
+          float r2[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float send = b3 ? r4[q] : r4[q + 2];
+            r2[q] = (b3 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, send, 8);
+          }
+          float r1 = (b2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r2[0] : r2[1], 4);
+          r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+          r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+          if ((lane & 3) == 0)
+            atomicAdd(&red[c / 2 + (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)], r1);
+        }
+        epi_sync(half);
+        const int s = ea.z_site[z];
+        const int nx = ea.xcnt[s];
+        const int nv = n_valid[z];
+        for (int k = c_lo / 2 + te; k < c_hi / 2; k += 128) {
+          const int r = n0 / 2 + k;
+          if (2 * r < nv) {
+            const int ix = ea.xlist[ea.xoff[s] + r % nx];
+            const int iy = ea.ylist[ea.yoff[s] + r / nx];
+            const int64_t idx = ((int64_t)ea.z_type[z] * ea.n_sy + iy) * ea.n_sx + ix;
+            atomicAdd(ea.map + idx, (double)red[k]);
+          }
+        }
+        epi_sync(half);
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty + b);
+      ++i;
+    }
+  }
+  __syncwarp();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, 2 * BN);
+  if (!ok && status) atomicExch(status, 1);
+}
+
 // A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]]
 template <int PREC>
 __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out, int w,
@@ -598,10 +891,52 @@ cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!count[dev] &&
+      cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    count[dev] = 148;
+  return count[dev];
+}
+
+// Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
+// kernel for TF32, one CTA per tile for BF16 hi + lo.
+template <int MODE, int PREC>
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int kblocks, int gx, int gy,
+                        int gz, const int* tile_prefix, const int* a_batch, const int* b_batch,
+                        const int* n_valid, const int* m_valid, const EpiStore& es,
+                        const EpiAbs2& ea, const EpiSpread& ey, int* status, cudaStream_t st,
+                        int valid_tiles) {
+  if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
+  if constexpr (PREC == EELS_TC_TF32) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_ws<MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ws::smem<MODE>());
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
+    if (tiles <= 0) return cudaSuccess;
+    const int grid = std::min(tiles, sm_count());
+    k_tc_gemm_ws<MODE><<<grid, ws::THREADS, ws::smem<MODE>(), st>>>(
+        ta, tb, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
+        status);
+  } else {
+    cudaError_t e = set_attrs<PREC>();
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<MODE, PREC><<<dim3(gx, gy, gz), 128, smem_of<MODE, PREC>(), st>>>(
+        ta, tb, kblocks, a_batch, b_batch, n_valid, m_valid, es, ea, ey, status);
+  }
+  return cudaGetLastError();
+}
+
 template <int PREC>
 cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mA1, mB1;
   if ((e = make_map<PREC>(&mA1, b.A1, b.k1p, b.n_out, b.slots_cap, BM)) != cudaSuccess) return e;
   if ((e = make_map<PREC>(&mB1, b.B1, b.k1p, 2 * b.n_in, b.slots_cap * b.n_types, BN)) !=
@@ -611,17 +946,14 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   EpiStore es{b.M1, Prec<PREC>::PLANES * pstride, pstride, b.k2p, b.n_out, b.k2p};
   EpiAbs2 ea{};
   EpiSpread ey{};
-  dim3 g1((b.k2p + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<0, PREC><<<g1, 128, smem_of<0, PREC>(), st>>>(mA1, mB1, b.k1p / Prec<PREC>::BK,
-                                                         b.a_batch1, b.b_batch1, b.n_valid1, nullptr,
-                                                         es, ea, ey, b.status);
-  return cudaGetLastError();
+  return launch_gemm<0, PREC>(mA1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
+                              (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, nullptr, b.a_batch1,
+                              b.b_batch1, b.n_valid1, nullptr, es, ea, ey, b.status, st, 0);
 }
 
 template <int PREC>
 cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mM1, mB2;
   if ((e = make_map<PREC>(&mM1, b.M1, b.k2p, b.n_out, b.slots_cap * b.n_types, BM)) !=
       cudaSuccess)
@@ -632,11 +964,10 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  dim3 g2((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<1, PREC><<<g2, 128, smem_of<1, PREC>(), st>>>(mM1, mB2, b.k2p / Prec<PREC>::BK,
-                                                         b.a_batch2, b.b_batch2, b.n_valid2, nullptr,
-                                                         es, ea, ey, b.status);
-  return cudaGetLastError();
+  return launch_gemm<1, PREC>(mM1, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+                              (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
+                              b.a_batch2, b.b_batch2, b.n_valid2, nullptr, es, ea, ey, b.status,
+                              st, b.n_tiles_v);
 }
 
 // Association with the probe sum first: gathers for GEMM-Y (A1 is shared with GEMM-V).
@@ -660,7 +991,6 @@ cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
 template <int PREC>
 cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mAY, mBY;
   if ((e = make_map<PREC>(&mAY, b.AY, b.k2p, b.nr_cap, b.slots_cap, BM)) != cudaSuccess) return e;
   if ((e = make_map<PREC>(&mBY, b.BY, b.k2p, b.k1p, b.slots_cap, BN)) != cudaSuccess) return e;
@@ -669,17 +999,15 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{};
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
                b.n_types, b.H, b.h_mul, b.slot_site};
-  dim3 g((b.k1p + BN - 1) / BN, (b.nr_cap + BM - 1) / BM, b.n_sites);
-  k_tc_gemm<2, PREC><<<g, 128, smem_of<2, PREC>(), st>>>(mAY, mBY, b.k2p / Prec<PREC>::BK,
-                                                        b.a_batch_y, b.a_batch_y, b.n_valid_y,
-                                                        b.m_valid_y, es, ea, ey, b.status);
-  return cudaGetLastError();
+  return launch_gemm<2, PREC>(mAY, mBY, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
+                              (b.nr_cap + BM - 1) / BM, b.n_sites, b.tiles_y, b.a_batch_y,
+                              b.a_batch_y, b.n_valid_y, b.m_valid_y, es, ea, ey, b.status, st,
+                              b.n_tiles_y);
 }
 
 template <int PREC>
 cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  if ((e = set_attrs<PREC>()) != cudaSuccess) return e;
   CUtensorMap mA1, mBV;
   if ((e = make_map<PREC>(&mA1, b.A1, b.k1p, b.n_out, b.slots_cap, BM)) != cudaSuccess) return e;
   if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, BN)) !=
@@ -689,11 +1017,10 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  dim3 g((2 * b.nr_cap + BN - 1) / BN, (b.n_out + BM - 1) / BM, b.n_sites * b.n_types);
-  k_tc_gemm<1, PREC><<<g, 128, smem_of<1, PREC>(), st>>>(mA1, mBV, b.k1p / Prec<PREC>::BK,
-                                                        b.a_batch1, b.b_batch1, b.n_valid2, nullptr,
-                                                        es, ea, ey, b.status);
-  return cudaGetLastError();
+  return launch_gemm<1, PREC>(mA1, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+                              (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
+                              b.a_batch1, b.b_batch1, b.n_valid2, nullptr, es, ea, ey, b.status,
+                              st, b.n_tiles_v);
 }
 
 }  // namespace

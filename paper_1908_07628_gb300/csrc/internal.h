@@ -134,6 +134,12 @@ struct TcBatch {
   const int* a_batch_y; const int* n_valid_y;   // identity map and k1p per site
   const int* m_valid_y;                         // scan positions of the site of each slot
   const float2* axT; const float2* ayT;         // phase tables [pos][n_in] (transposed)
+  // prefix sums of the tiles with work per problem (the persistent TF32 GEMMs walk only
+  // those): tiles_v over the transitions for GEMM 2 / GEMM-V (column tiles of 2 n_R rows x
+  // all row tiles of n_out), tiles_y over the sites for GEMM-Y (row tiles of n_R x all
+  // column tiles); n_tiles_* = the batch's total
+  const int* tiles_v; int n_tiles_v;
+  const int* tiles_y; int n_tiles_y;
 };
 cudaError_t tc_gather(const TcBatch& b, cudaStream_t s);   // A1, B1, B2 operand buffers
 cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t s);    // M1 = GEMM 1
