@@ -488,7 +488,8 @@ def gpu_arm(args, rank, world):
             peak = bf16_peak * TF32_PER_BF16
             achieved = flops / per_step / avg_s / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": measured_traffic(dom, wl.n, "batch"),
                     "peak_source": bf16_src + " x nominal tf32/bf16 (1.1/2.25)"}
         else:
             flops = contraction_flops(wl, n_in, n_out, dom)
