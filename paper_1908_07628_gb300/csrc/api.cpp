@@ -37,6 +37,7 @@ struct eels_ctx {
 
 struct eels_smatrix {
   eels_ctx* ctx = nullptr;
+  int device = 0;              // freeing the handle must not depend on the context
   int n = 0, n_z = 0, f = 1;
   double cell = 0, lam = 0, sigma = 0, dz = 0, alpha = 0;
   std::vector<int> bp, bq;     // probe beams, f-lattice integer indices
@@ -86,6 +87,16 @@ struct Prof {
     return e;
   }
 };
+
+// Select the context's device and drop a non-sticky error another library (or an
+// unrelated failed call) left on this thread, so that the launch checks of this call
+// report only this call's failures.  A sticky error (a faulted context) persists and
+// is reported by the next CUDA call anyway.
+cudaError_t enter(const eels_ctx* ctx) {
+  const cudaError_t e = cudaSetDevice(ctx->device);
+  (void)cudaGetLastError();
+  return e;
+}
 
 #define EELS_CK(call)                                          \
   do {                                                         \
@@ -221,6 +232,7 @@ void eels_destroy(eels_ctx* ctx) {
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->spare) cudaEventDestroy(e);
   delete ctx;
+  (void)cudaGetLastError();
 }
 
 const char* eels_last_error(const eels_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
@@ -327,7 +339,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
   *out = nullptr;
   eels_status r = check_specimen(ctx, spec, op);
   if (r != EELS_OK) return r;
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int n = spec->n, nh = n / 2, n_z = spec->n_z;
   std::vector<int> bp, bq;
@@ -341,6 +353,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
 
   eels_smatrix* sm = new eels_smatrix();
   sm->ctx = ctx;
+  sm->device = ctx->device;
   sm->n = n; sm->n_z = n_z; sm->f = op->f;
   sm->cell = spec->cell; sm->lam = op->lambda; sm->sigma = op->sigma; sm->dz = op->dz;
   sm->alpha = op->alpha;
@@ -404,13 +417,14 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
 
 void eels_smatrix_free(eels_smatrix* sm) {
   if (!sm) return;
-  cudaSetDevice(sm->ctx->device);
+  cudaSetDevice(sm->device);
   cudaStreamSynchronize(sm->st);
   if (sm->t) cudaFreeAsync(sm->t, sm->st);
   if (sm->ptab) cudaFreeAsync(sm->ptab, sm->st);
   if (sm->s_exit) cudaFreeAsync(sm->s_exit, sm->st);
   if (sm->s_in) cudaFreeAsync(sm->s_in, sm->st);
   delete sm;
+  (void)cudaGetLastError();   // a void call leaves no error for the caller's next call
 }
 
 eels_status eels_smatrix_info(const eels_smatrix* sm, int* n, int* n_z, int* n_in) {
@@ -430,7 +444,7 @@ eels_status eels_smatrix_beams(const eels_smatrix* sm, int32_t* p, int32_t* q) {
 eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* dst, void* stream) {
   if (!sm || !dst || depth < 0 || depth >= sm->n_z) return EELS_ERR_ARG;
   eels_ctx* ctx = sm->ctx;
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   const int64_t per = (int64_t)sm->bp.size() * (sm->n / 2) * (sm->n / 2);
   EELS_CK(cudaMemcpyAsync(dst, sm->s_in + depth * per, per * sizeof(float2),
                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
@@ -494,7 +508,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   const bool tc = precision != EELS_PREC_FP32;
   const int tc_prec = precision == EELS_PREC_BF16X3 ? EELS_TC_BF16X3 : EELS_TC_TF32;
   if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int n = sm->n, nh = n / 2, n_z = sm->n_z, f = sm->f;
   const int n_in = (int)sm->bp.size();
@@ -960,7 +974,7 @@ eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eel
   for (int d = 0; d < n_det; ++d)
     if (!(det[d].inner >= 0) || det[d].outer != det[d].outer)
       return fail(ctx, EELS_ERR_ARG, "bad detector angles");
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int n_in = (int)sm->bp.size();
   const int64_t n_img = (int64_t)sc->n_sx * sc->n_sy;
@@ -1042,7 +1056,7 @@ eels_status eels_phonon_map(eels_ctx* ctx, const eels_specimen* specs,
   for (int c = 1; c < n_configs; ++c)
     if (specs[c].n != specs[0].n || trs[c].n_types != trs[0].n_types)
       return fail(ctx, EELS_ERR_ARG, "configurations differ in grid or channel count");
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n_map = (int64_t)trs[0].n_types * sc->n_sx * sc->n_sy;
   DevBuf<double> acc, one;
@@ -1070,7 +1084,7 @@ eels_status eels_phonon_map(eels_ctx* ctx, const eels_specimen* specs,
 eels_status eels_divide_map(eels_ctx* ctx, double* map, const double* bf, int n_types,
                             int64_t n_pix, int on_device, void* stream) {
   if (!ctx || !map || !bf || n_types < 0 || n_pix < 0) return fail(ctx, EELS_ERR_ARG, "bad arguments");
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   if (on_device) {
     EELS_CK(eels::launch_divide(map, bf, n_types, n_pix, st));
@@ -1095,7 +1109,7 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
   if (r != EELS_OK) return r;
   if ((r = check_transitions(ctx, tr, sc, spec->n, spec->n_z)) != EELS_OK) return r;
   if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
-  EELS_CK(cudaSetDevice(ctx->device));
+  EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int n = spec->n, nh = n / 2, n_z = spec->n_z, f = op->f;
   const int T = tr->n_types, w = tr->w, S = tr->n_sites;

@@ -139,6 +139,7 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
   const size_t o_phi = align256(o_w + wave_bytes * chunk);
 
   unsigned char* base = nullptr;
+  (void)cudaGetLastError();   // drop a non-sticky error left by unrelated earlier calls
   cudaError_t e = scratch_ptr(&base);
   if (e != cudaSuccess) {
     set_err(err, err_cap, cudaGetErrorString(e));
