@@ -17,9 +17,9 @@
 //           planes); each product is lo*hi + hi*lo + hi*hi with kind::f16 MMAs into
 //           the same FP32 accumulator (the lo*lo term is below FP32 resolution).
 // Operands are gathered into K-padded buffers [batch][plane][rows][K] and streamed
-// by TMA (128-byte swizzle) through an mbarrier pipeline.  TF32 runs a persistent,
-// warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws);
-// BF16 hi + lo runs one 128 x 256 tile per CTA (k_tc_gemm): warp 0 lane 0 issues TMA,
+// by TMA (128-byte swizzle) through an mbarrier pipeline.  The GEMMs run a persistent,
+// warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws); GEMM-Y
+// in BF16 hi + lo runs one 128 x 256 tile per CTA (k_tc_gemm): warp 0 lane 0 issues TMA,
 // warp 1 lane 0 issues MMA, all four warps drain TMEM in the epilogue.
 #include <algorithm>
 
@@ -405,13 +405,17 @@ constexpr int CW = 32;                          // GEMM-Y epilogue chunk (column
 constexpr int PITCH = CW * 4 + 16;              // staging row pitch (bytes)
 constexpr int TILE = 2 * BM * PITCH;            // one channel of a chunk
 constexpr int TG = 1;                           // channels staged at once per column half
-template <int MODE>
-__host__ __device__ constexpr int stages() { return MODE == 2 ? 3 : 4; }
+// TF32 stages are 48 KB (4, or 3 beside the GEMM-Y staging); BF16 hi + lo stages are
+// 96 KB (2).  GEMM-Y runs here in TF32 only.
+template <int MODE, int PREC>
+__host__ __device__ constexpr int stages() {
+  return PREC == EELS_TC_TF32 ? (MODE == 2 ? 3 : 4) : 2;
+}
 template <int MODE>
 __host__ __device__ constexpr size_t staging() { return MODE == 2 ? (size_t)2 * TG * TILE : 0; }
-template <int MODE>
+template <int MODE, int PREC>
 __host__ __device__ constexpr size_t smem() {
-  return (size_t)stages<MODE>() * Tile<EELS_TC_TF32>::STAGE_BYTES + staging<MODE>() + 1024 + 256;
+  return (size_t)stages<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + staging<MODE>() + 1024 + 256;
 }
 }  // namespace ws
 
@@ -420,16 +424,17 @@ __device__ __forceinline__ void epi_sync(int half) {
   asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
 }
 
-template <int MODE>
+template <int MODE, int PREC>
 __global__ void __launch_bounds__(ws::THREADS, 1)
 k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
              int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
              const int* __restrict__ a_batch, const int* __restrict__ b_batch,
              const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
              EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
-  using P = Prec<EELS_TC_TF32>;
-  using TL = Tile<EELS_TC_TF32>;
-  constexpr int S = ws::stages<MODE>(), BK = P::BK;
+  static_assert(MODE != 2 || PREC == EELS_TC_TF32, "GEMM-Y runs the persistent form in TF32");
+  using P = Prec<PREC>;
+  using TL = Tile<PREC>;
+  constexpr int S = ws::stages<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ float red[BN / 2];
   __shared__ int abort_flag;
@@ -506,8 +511,12 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           if (it >= S && !(ok = tc::mbar_wait(empty + s, ((it / S) - 1) & 1))) break;
           uint8_t* st = sm + s * TL::STAGE_BYTES;
           tc::mbar_arrive_expect_tx(full + s, TL::STAGE_BYTES);
-          tc::tma_load_4d(st, &ta, full + s, kb * BK, m0, 0, ab);
-          tc::tma_load_4d(st + TL::A_BYTES, &tb, full + s, kb * BK, n0, 0, bb);
+#pragma unroll
+          for (int pl = 0; pl < PL; ++pl) {
+            tc::tma_load_4d(st + pl * TL::A_BYTES, &ta, full + s, kb * BK, m0, pl, ab);
+            tc::tma_load_4d(st + PL * TL::A_BYTES + pl * TL::B_BYTES, &tb, full + s, kb * BK, n0,
+                            pl, bb);
+          }
         }
       }
       // the last load of every stage has landed before the CTA may leave
@@ -528,11 +537,22 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           if (!(ok = tc::mbar_wait(full + s, (it / S) & 1))) break;
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(sm + s * TL::STAGE_BYTES);
-          const uint32_t sb = sa + TL::A_BYTES;
+          const uint32_t sb = sa + PL * TL::A_BYTES;
+          // each MMA consumes 32 bytes of K: 8 TF32 or 16 BF16 elements
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_tf32(d, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32), P::IDESC,
-                         (kb | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+            if constexpr (PREC == EELS_TC_TF32) {
+              tc::mma_tf32(d, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32),
+                           P::IDESC, acc);
+            } else {
+              const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
+              const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
+              tc::mma_f16(d, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
+              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
+              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
+            }
+          }
           tc::mma_commit(empty + s);
         }
         if (!ok) break;
@@ -570,7 +590,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           tc::tmem_ld16(trow + c, v);
           const int col = n0 + c;
           if (row < es.rows && col < es.cols)
-            put16<EELS_TC_TF32>(es.out, es.plane_stride, rbase + col, v);
+            put16<PREC>(es.out, es.plane_stride, rbase + col, v);
         }
       } else if constexpr (MODE == 2) {
         const int site = ey.slot_site[z];
@@ -902,7 +922,7 @@ int sm_count() {
 }
 
 // Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
-// kernel for TF32, one CTA per tile for BF16 hi + lo.
+// kernel, except GEMM-Y in BF16 hi + lo (one CTA per tile).
 template <int MODE, int PREC>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int kblocks, int gx, int gy,
                         int gz, const int* tile_prefix, const int* a_batch, const int* b_batch,
@@ -910,19 +930,19 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int kblock
                         const EpiAbs2& ea, const EpiSpread& ey, int* status, cudaStream_t st,
                         int valid_tiles) {
   if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
-  if constexpr (PREC == EELS_TC_TF32) {
+  if constexpr (PREC == EELS_TC_TF32 || MODE != 2) {
     static bool attr = false;
     if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_ws<MODE>,
+      cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_ws<MODE, PREC>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ws::smem<MODE>());
+                                           (int)ws::smem<MODE, PREC>());
       if (e != cudaSuccess) return e;
       attr = true;
     }
     const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
     if (tiles <= 0) return cudaSuccess;
     const int grid = std::min(tiles, sm_count());
-    k_tc_gemm_ws<MODE><<<grid, ws::THREADS, ws::smem<MODE>(), st>>>(
+    k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
         ta, tb, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
         status);
   } else {
