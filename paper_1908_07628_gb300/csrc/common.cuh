@@ -25,11 +25,12 @@ __device__ __forceinline__ float2 mul_i(float2 a) {
 }
 
 // ---------------------------------------------------------------------------
-// Radix plans.  Two-stage plans with in-register radix-16/32 butterflies for the common
-// power-of-two grids (one shared-memory exchange per transform).
+// Radix plans.  Two-stage plans with in-register radix-16/24/32 butterflies for the
+// common grids 256, 512, 768, 1024 (one shared-memory exchange per transform).
 __host__ __device__ constexpr int plan2_radix(int n, int s) {
   return n == 256 ? (s < 2 ? 16 : 0)
        : n == 512 ? (s == 0 ? 16 : s == 1 ? 32 : 0)
+       : n == 768 ? (s == 0 ? 24 : s == 1 ? 32 : 0)
        : n == 1024 ? (s < 2 ? 32 : 0)
        : -1;
 }
@@ -157,12 +158,34 @@ __host__ __device__ constexpr float cos32(int m) {
 }
 __host__ __device__ constexpr float sin32(int m) { return cos32(m - 8); }
 
+// exp(2 pi i m / 24) components (multiples of 15 degrees)
+__host__ __device__ constexpr float cos24(int m) {
+  constexpr float c[24] = {1.0f, 9.659258263e-01f, 8.660254038e-01f, 7.071067812e-01f, 0.5f,
+                           2.588190451e-01f, 0.0f, -2.588190451e-01f, -0.5f, -7.071067812e-01f,
+                           -8.660254038e-01f, -9.659258263e-01f, -1.0f, -9.659258263e-01f,
+                           -8.660254038e-01f, -7.071067812e-01f, -0.5f, -2.588190451e-01f, 0.0f,
+                           2.588190451e-01f, 0.5f, 7.071067812e-01f, 8.660254038e-01f,
+                           9.659258263e-01f};
+  return c[((m % 24) + 24) % 24];
+}
+__host__ __device__ constexpr float sin24(int m) { return cos24(m - 6); }
+
+// exp(sg 2 pi i m / R) for R dividing 32 or 24
+template <int R>
+__device__ __forceinline__ float2 croot(int m, float sg) {
+  if constexpr (32 % R == 0) {
+    return make_float2(cos32(m * (32 / R)), sg * sin32(m * (32 / R)));
+  } else {
+    static_assert(24 % R == 0, "composite radix must divide 32 or 24");
+    return make_float2(cos24(m * (24 / R)), sg * sin24(m * (24 / R)));
+  }
+}
+
 // In-register DFT of length R = R1 R2: n = R2 n1 + n2, k = k1 + R1 k2;
 // DFT_R1 over n1, twiddle exp(+-2 pi i n2 k1 / R), DFT_R2 over n2.
 template <int R1, int R2, bool INV>
 __device__ __forceinline__ void dft_composite(float2* x) {
   constexpr int R = R1 * R2;
-  constexpr int SC = 32 / R;
   constexpr float SG = INV ? 1.f : -1.f;
   float2 y[R];
 #pragma unroll
@@ -174,8 +197,7 @@ __device__ __forceinline__ void dft_composite(float2* x) {
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const int m = (n2 * k1) % R;
-      y[n2 * R1 + k1] = m == 0 ? t[k1]
-                               : cmul(t[k1], make_float2(cos32(m * SC), SG * sin32(m * SC)));
+      y[n2 * R1 + k1] = m == 0 ? t[k1] : cmul(t[k1], croot<R>(m, SG));
     }
   }
 #pragma unroll
@@ -192,6 +214,10 @@ template <>
 __device__ __forceinline__ void dft<16, false>(float2* u) { dft_composite<4, 4, false>(u); }
 template <>
 __device__ __forceinline__ void dft<16, true>(float2* u) { dft_composite<4, 4, true>(u); }
+template <>
+__device__ __forceinline__ void dft<24, false>(float2* u) { dft_composite<8, 3, false>(u); }
+template <>
+__device__ __forceinline__ void dft<24, true>(float2* u) { dft_composite<8, 3, true>(u); }
 template <>
 __device__ __forceinline__ void dft<32, false>(float2* u) { dft_composite<8, 4, false>(u); }
 template <>

@@ -27,11 +27,11 @@ constexpr int kRowWarps = 8;   // rows per CTA in the row pass
 constexpr int kColCB = 8;      // columns per CTA in the column pass (one warp each)
 
 template <int N>
-__global__ void __launch_bounds__(kRowWarps * 32)
-k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
-           const float2* __restrict__ t_slice, int conj_t, int store_mode,
-           float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
-           const float2* __restrict__ tw) {
+__device__ __forceinline__ void row_pass_body(const float2* __restrict__ W, float2* __restrict__ Phi,
+                                              const float2* __restrict__ t_slice, int conj_t,
+                                              int store_mode, float2* __restrict__ S, int s_waves,
+                                              int64_t s_stride, int fft_out,
+                                              const float2* __restrict__ tw) {
   constexpr int NH = N / 2, NQ = N / 4;
   constexpr int ROWS = RegFFT<N>::ROWS;
   constexpr int LDR = spad_len(N);
@@ -110,6 +110,26 @@ k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
       }
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRowWarps * 32)
+k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
+           const float2* __restrict__ t_slice, int conj_t, int store_mode,
+           float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
+           const float2* __restrict__ tw) {
+  row_pass_body<N>(W, Phi, t_slice, conj_t, store_mode, S, s_waves, s_stride, fft_out, tw);
+}
+
+// The 768 plan (radix 24 then 32) would take 132 registers and so one CTA per SM; this
+// form caps it at 128 (two CTAs) without spills.
+template <int N>
+__global__ void __launch_bounds__(kRowWarps * 32, 2)
+k_row_pass_2cta(const float2* __restrict__ W, float2* __restrict__ Phi,
+                const float2* __restrict__ t_slice, int conj_t, int store_mode,
+                float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
+                const float2* __restrict__ tw) {
+  row_pass_body<N>(W, Phi, t_slice, conj_t, store_mode, S, s_waves, s_stride, fft_out, tw);
 }
 
 // Padding period of the column tile: the forward transform's first stage reads
@@ -391,12 +411,15 @@ cudaError_t row_pass_n(int n_waves, const float2* W, float2* Phi, const float2* 
                        const float2* tw, cudaStream_t s) {
   constexpr int ROWS = RegFFT<N>::ROWS;
   const size_t smem = (size_t)kRowWarps * ROWS * spad_len(N) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_row_pass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  auto kern = [] {
+    if constexpr (N == 768) return k_row_pass_2cta<N>;
+    else return k_row_pass<N>;
+  }();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(N / (kRowWarps * ROWS), n_waves);
-  k_row_pass<N><<<grid, kRowWarps * 32, smem, s>>>(W, Phi, t, conj_t, store_mode, S, s_waves,
-                                                   s_stride, fft_out, tw);
+  kern<<<grid, kRowWarps * 32, smem, s>>>(W, Phi, t, conj_t, store_mode, S, s_waves, s_stride,
+                                          fft_out, tw);
   return cudaGetLastError();
 }
 

@@ -400,3 +400,39 @@ def test_phonon_average_matches_oracle(g, ctx):
         ctx.phonon_map([cfg[0], sp.rocksalt_phonons(1, ncell=2, nzc=3, n=256, f=2, scan_n=4,
                                                      w=16)[0]])
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n,f,seed", [(768, 2, 21), (768, 3, 22)])
+def test_s_in_and_map_at_768(g, ctx, n, f, seed):
+    """The 768 grid's two-stage plan (radix 24, then 32): S_in at every depth and the map.
+    A 15.4 A cell keeps the FP64 oracle's beam arrays near a gigabyte."""
+    import torch
+    wl = _rand(n, f, seed, n_z=2, n_sites=4, w=12, cell=n * 0.02)
+    s_in, beams = lin.build_s_in(wl)
+    sm = g.build_smatrix_for(ctx, wl)
+    nh = n // 2
+    for depth in range(wl.n_z):
+        out = torch.empty((sm.n_in, nh, nh), dtype=torch.complex64, device="cuda")
+        sm.copy_depth(depth, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.complex128) / n
+        err = np.linalg.norm(got - s_in[depth]) / np.linalg.norm(s_in[depth])
+        assert err < 1e-5, (depth, err)
+    # the FFT plan is what this checks: the map through the FP32 contraction (the
+    # tensor-core contractions are checked on the other grids)
+    ref = lin.linear_map(wl, s_in=(s_in, beams))
+    assert ref.max() > 0
+    assert eps(ref, g.inelastic_map_for(ctx, sm, wl, "fp32")) < EPS_FP32
+
+
+def test_handle_freed_after_its_context(g):
+    """A garbage collector may finalise a context before the S-matrix built on it; the
+    handle must still free cleanly and leave no error for the next call."""
+    wl = _rand(64, 1, 23)
+    c = g.Context(0)
+    sm = g.build_smatrix_for(c, wl)
+    c.close()
+    sm.free()
+    c2 = g.Context(0)
+    got = g.inelastic_map_for(c2, g.build_smatrix_for(c2, wl), wl, "fp32")
+    assert eps(ms.quadratic_map(wl), got) < EPS_FP32
