@@ -122,7 +122,9 @@ const char* eels_last_error(const eels_ctx* ctx);
 eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const eels_optics* optics,
                                void* stream, eels_smatrix** out);
 /* Releases the handle in stream order on the stream it was built on, which must
- * still exist; the call waits for that stream's queued work first. */
+ * still exist; the call waits for that stream's queued work first.  The context the
+ * handle was built on may already be destroyed (language bindings whose garbage
+ * collector finalises objects in any order rely on this). */
 void eels_smatrix_free(eels_smatrix* sm);
 
 /* Shape of a built S-matrix: grid, slices and number of probe beams. */
