@@ -171,20 +171,24 @@ def cpu_oracle_rate(wl_name, budget_procs=None):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def _algorithmic(wl, n_in, n_out, prof):
-    """Algorithmic bytes / flops per launch of each kernel class (design notes)."""
-    n = wl.n
+def _algorithmic(wl, n_in, n_out, prof, steps):
+    """Algorithmic bytes of the multislice kernels per step of the default (stream)
+    scheme.  Row pass: read W and write Phi (N x N/2 each) and store the even samples
+    ((N/2)^2) per wave, plus the slice's t (N^2) once per launch; the last slice of each
+    sweep stores without writing Phi.  Column pass: read Phi, write W.  Complex64."""
+    n, nz = wl.n, wl.n_z
     nh = n // 2
-    cplx = 8
+    c = 8
+    row = (2 * n * nh + nh * nh) * c
+    last = (n * nh + nh * nh) * c
+    col = 2 * n * nh * c
+    t = n * n * c
     out = {}
-    # row pass: read W + write Phi (n x n/2 per wave), store n/2 x n/2 per wave, read t once
     for name, waves in (("row_pass", n_in), ("row_pass_adjoint", n_out)):
-        out[name] = ("hbm", waves * (2 * n * nh + nh * nh) * cplx + n * n * cplx)
-    out["row_pass_inverse"] = ("hbm", n_out * 2 * n * nh * cplx + n * n * cplx)
-    out["row_pass_store"] = ("hbm", n_out * (n * nh + nh * nh) * cplx)
-    for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out),
-                        ("col_pass_inverse", n_out), ("col_pass_band", n_out)):
-        out[name] = ("hbm", waves * 2 * n * nh * cplx)
+        launches = prof.get(name, {}).get("launches", 0) / steps
+        out[name] = ("hbm", waves * ((nz - 1) * row + last) + launches * t)
+    for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out)):
+        out[name] = ("hbm", waves * (nz - 1) * col)
     return out
 
 
@@ -457,7 +461,7 @@ def gpu_arm(args, rank, world):
     bf16_peak = peaks["bf16_tflops"] if unthrottled else peaks["bf16_tflops_sustained"]
     bf16_src = ("measured bf16 burst (clocks at max, no power cap)" if unthrottled
                 else "measured bf16 sustained")
-    alg = _algorithmic(wl, n_in, n_out, prof)
+    alg = _algorithmic(wl, n_in, n_out, prof, args.steps)
     tot = {k: v["ms"] for k, v in prof.items()}
     dom = max(tot, key=tot.get) if tot else None
     roof = None
@@ -466,12 +470,14 @@ def gpu_arm(args, rank, world):
         avg_s = prof[dom]["ms"] / launches / 1e3
         per_step = launches / args.steps          # launches of this kernel in one step
         if dom in alg and alg[dom][0] == "hbm":
-            achieved = alg[dom][1] / avg_s / 1e9
+            # per step = per launch x launches per step, for bytes and time alike
+            bytes_launch = alg[dom][1] / per_step
+            achieved = bytes_launch / avg_s / 1e9
             waves = n_out if "adjoint" in dom else n_in
             roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                     "traffic": measured_traffic(dom, wl.n, waves),
-                    "algorithmic_bytes": alg[dom][1],
+                    "algorithmic_bytes": bytes_launch,
                     "peak_source": "measured" if "fallback" not in peaks else "fallback"}
         elif "bf16x3" in dom:
             useful = contraction_flops(wl, n_in, n_out, dom)
@@ -499,6 +505,10 @@ def gpu_arm(args, rank, world):
             roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
+    # every multislice kernel against the HBM bound (the dominant one is in roofline)
+    hbm = {k: {"achieved_gbs": alg[k][1] / (prof[k]["ms"] / args.steps / 1e3) / 1e9,
+               "frac": alg[k][1] / (prof[k]["ms"] / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"]}
+           for k in alg if k in prof and prof[k]["ms"] > 0}
     share = {k: {"launches": prof[k]["launches"], "ms_per_step": prof[k]["ms"] / args.steps,
                  "share": prof[k]["ms"] / max(sum(tot.values()), 1e-9)} for k in prof}
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
@@ -516,6 +526,7 @@ def gpu_arm(args, rank, world):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": roof,
+        "multislice_hbm": hbm,
         "kernels": share,
         "clocks": clk,
         "gpu_quadratic": quad,
