@@ -505,10 +505,31 @@ def gpu_arm(args, rank, world):
             roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
-    # every multislice kernel against the HBM bound (the dominant one is in roofline)
-    hbm = {k: {"achieved_gbs": alg[k][1] / (prof[k]["ms"] / args.steps / 1e3) / 1e9,
-               "frac": alg[k][1] / (prof[k]["ms"] / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"]}
-           for k in alg if k in prof and prof[k]["ms"] > 0}
+    # every multislice kernel against the HBM bound (the dominant one is in roofline) and
+    # against the FP32 ALU bound: per wave and slice the row pass runs two N-point FFTs on
+    # N rows and one complex multiply per pixel (10 N^2 log2 N + 6 N^2 flop), the column
+    # pass two N-point FFTs on the N/2 band columns and the propagator multiply
+    # (5 N^2 log2 N + 3 N^2 flop)
+    mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES * 2 * mhz * 1e6
+    lg = math.log2(wl.n)
+    nn = float(wl.n) ** 2
+    # (the last row pass of each sweep stops after the inverse FFT and the multiply)
+    row_full, row_last = 10 * nn * lg + 6 * nn, 5 * nn * lg + 6 * nn
+    col = 5 * nn * lg + 3 * nn
+    fft = {"row_pass": n_in * ((wl.n_z - 1) * row_full + row_last),
+           "row_pass_adjoint": n_out * ((wl.n_z - 1) * row_full + row_last),
+           "col_pass": n_in * (wl.n_z - 1) * col,
+           "col_pass_adjoint": n_out * (wl.n_z - 1) * col}
+    hbm = {}
+    for k in alg:
+        if k not in prof or prof[k]["ms"] <= 0:
+            continue
+        sec = prof[k]["ms"] / args.steps / 1e3
+        hbm[k] = {"achieved_gbs": alg[k][1] / sec / 1e9,
+                  "frac": alg[k][1] / sec / 1e9 / peaks["hbm_gbs"],
+                  "fft_tflops": fft[k] / sec / 1e12,
+                  "fp32_frac": fft[k] / sec / fp32_peak}
     share = {k: {"launches": prof[k]["launches"], "ms_per_step": prof[k]["ms"] / args.steps,
                  "share": prof[k]["ms"] / max(sum(tot.values()), 1e-9)} for k in prof}
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
