@@ -401,9 +401,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 namespace ws {
 constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter, one per column half
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int CW = 32;                          // GEMM-Y epilogue chunk (columns)
-constexpr int PITCH = CW * 4 + 16;              // staging row pitch (bytes)
-constexpr int TILE = 2 * BM * PITCH;            // one channel of a chunk
+constexpr int CW = 32;                          // GEMM-Y epilogue chunk (columns, 128 B)
+constexpr int TILE = 2 * BM * CW * 4;           // one chunk of one channel: 256 rows x 128 B,
+                                                // 128-byte swizzled, stored by one TMA box
 constexpr int TG = 1;                           // channels staged at once per column half
 // TF32 stages are 48 KB (4, or 3 beside the GEMM-Y staging); BF16 hi + lo stages are
 // 96 KB (2).  GEMM-Y runs here in TF32 only.
@@ -427,7 +427,7 @@ __device__ __forceinline__ void epi_sync(int half) {
 template <int MODE, int PREC>
 __global__ void __launch_bounds__(ws::THREADS, 1)
 k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-             int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
+             const __grid_constant__ CUtensorMap tv, int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
              const int* __restrict__ a_batch, const int* __restrict__ b_batch,
              const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
              EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
@@ -593,48 +593,42 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             put16<PREC>(es.out, es.plane_stride, rbase + col, v);
         }
       } else if constexpr (MODE == 2) {
+        // chunks of 32 columns: each thread forms its two rows (H_t Y and -i H_t Y) in the
+        // half's staging tile (128-byte swizzled rows), and one thread of the half stores
+        // the tile with one TMA box; the tile is rewritten only after that store has read it
         const int site = ey.slot_site[z];
-        const int rows_out = 2 * ey.rows;
-        constexpr int SEGS = ws::CW * 4 / 16;
+        const int rr = 2 * (q4 * 32 + lane);
         for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += ws::CW) {
-          for (int t0 = 0; t0 < ey.n_types; t0 += ws::TG) {
-            const int tg = min(ws::TG, ey.n_types - t0);
+          for (int t0 = 0; t0 < ey.n_types; ++t0) {
             float v[ws::CW];
             tc::tmem_ld16(trow + c, v);
             tc::tmem_ld16(trow + c + 16, v + 16);
-            for (int tt = 0; tt < tg; ++tt) {
-              const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0 + tt) * ey.P;
-              uint8_t* d0 = stg_h + (size_t)tt * ws::TILE + (size_t)(2 * (q4 * 32 + lane)) * ws::PITCH;
-              float4* a = reinterpret_cast<float4*>(d0);
-              float4* bq = reinterpret_cast<float4*>(d0 + ws::PITCH);
+            if (te == 0) tc::bulk_wait_read();
+            epi_sync(half);
+            const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0) * ey.P;
+            uint8_t* r0 = stg_h + (size_t)rr * (ws::CW * 4);
+            uint8_t* r1 = r0 + ws::CW * 4;
 #pragma unroll
-              for (int q = 0; q < ws::CW / 4; ++q) {
-                const int pp = (n0 + c) / 2 + 2 * q;
-                const float2 h0 = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
-                const float2 h1 = pp + 1 < ey.P ? __ldg(Ht + pp + 1) : make_float2(0.f, 0.f);
-                const float2 y0 = cmul(h0, make_float2(v[4 * q], v[4 * q + 1]));
-                const float2 y1 = cmul(h1, make_float2(v[4 * q + 2], v[4 * q + 3]));
-                a[q] = make_float4(tc::to_tf32(y0.x), tc::to_tf32(y0.y), tc::to_tf32(y1.x),
-                                   tc::to_tf32(y1.y));
-                bq[q] = make_float4(tc::to_tf32(y0.y), tc::to_tf32(-y0.x), tc::to_tf32(y1.y),
-                                    tc::to_tf32(-y1.x));
-              }
+            for (int q = 0; q < ws::CW / 4; ++q) {
+              const int pp = (n0 + c) / 2 + 2 * q;
+              const float2 h0 = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
+              const float2 h1 = pp + 1 < ey.P ? __ldg(Ht + pp + 1) : make_float2(0.f, 0.f);
+              const float2 y0 = cmul(h0, make_float2(v[4 * q], v[4 * q + 1]));
+              const float2 y1 = cmul(h1, make_float2(v[4 * q + 2], v[4 * q + 3]));
+              // 16-byte chunk q of row r sits at chunk q ^ (r & 7) (128-byte swizzle)
+              *reinterpret_cast<float4*>(r0 + ((q ^ (rr & 7)) << 4)) =
+                  make_float4(tc::to_tf32(y0.x), tc::to_tf32(y0.y), tc::to_tf32(y1.x),
+                              tc::to_tf32(y1.y));
+              *reinterpret_cast<float4*>(r1 + ((q ^ ((rr + 1) & 7)) << 4)) =
+                  make_float4(tc::to_tf32(y0.y), tc::to_tf32(-y0.x), tc::to_tf32(y1.y),
+                              tc::to_tf32(-y1.x));
             }
+            tc::fence_async_shared();
             epi_sync(half);
-            const int items = tg * 2 * BM * SEGS;
-            for (int it2 = te; it2 < items; it2 += 128) {
-              const int part = it2 % SEGS;
-              const int rr = (it2 / SEGS) % (2 * BM);
-              const int tt = it2 / (SEGS * 2 * BM);
-              const int orow = 2 * m0 + rr;
-              if (orow >= rows_out) continue;
-              const int64_t e = ((int64_t)z * ey.n_types + t0 + tt) * ey.z_stride +
-                                (int64_t)orow * ey.row_pitch + n0 + c;
-              const uint4 val = *reinterpret_cast<const uint4*>(stg_h + (size_t)tt * ws::TILE +
-                                                                (size_t)rr * ws::PITCH + part * 16);
-              reinterpret_cast<uint4*>(static_cast<float*>(ey.bv) + e)[part] = val;
+            if (te == 0) {
+              tc::tma_store_4d(&tv, stg_h, n0 + c, 2 * m0, 0, z * ey.n_types + t0);
+              tc::bulk_commit();
             }
-            epi_sync(half);
           }
         }
       } else {
@@ -687,6 +681,9 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(acc_empty + b);
       ++i;
+    }
+    if constexpr (MODE == 2) {
+      if (te == 0) tc::bulk_wait();   // the CTA's TMA stores are complete before it leaves
     }
   }
   __syncwarp();
@@ -924,7 +921,8 @@ int sm_count() {
 // Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
 // kernel, except GEMM-Y in BF16 hi + lo (one CTA per tile).
 template <int MODE, int PREC>
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int kblocks, int gx, int gy,
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tv,
+                        int kblocks, int gx, int gy,
                         int gz, const int* tile_prefix, const int* a_batch, const int* b_batch,
                         const int* n_valid, const int* m_valid, const EpiStore& es,
                         const EpiAbs2& ea, const EpiSpread& ey, int* status, cudaStream_t st,
@@ -943,7 +941,7 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int kblock
     if (tiles <= 0) return cudaSuccess;
     const int grid = std::min(tiles, sm_count());
     k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
-        ta, tb, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
+        ta, tb, tv, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
         status);
   } else {
     cudaError_t e = set_attrs<PREC>();
@@ -966,7 +964,7 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   EpiStore es{b.M1, Prec<PREC>::PLANES * pstride, pstride, b.k2p, b.n_out, b.k2p};
   EpiAbs2 ea{};
   EpiSpread ey{};
-  return launch_gemm<0, PREC>(mA1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
+  return launch_gemm<0, PREC>(mA1, mB1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, nullptr, b.a_batch1,
                               b.b_batch1, b.n_valid1, nullptr, es, ea, ey, b.status, st, 0);
 }
@@ -984,7 +982,7 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  return launch_gemm<1, PREC>(mM1, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+  return launch_gemm<1, PREC>(mM1, mB2, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch2, b.b_batch2, b.n_valid2, nullptr, es, ea, ey, b.status,
                               st, b.n_tiles_v);
@@ -1019,7 +1017,12 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{};
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
                b.n_types, b.H, b.h_mul, b.slot_site};
-  return launch_gemm<2, PREC>(mAY, mBY, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
+  // store map of GEMM-Y's output: BV rows (2 per probe) in boxes of 32 columns x 256 rows
+  CUtensorMap mBV;
+  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, 2 * BM)) !=
+      cudaSuccess)
+    return e;
+  return launch_gemm<2, PREC>(mAY, mBY, mBV, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
                               (b.nr_cap + BM - 1) / BM, b.n_sites, b.tiles_y, b.a_batch_y,
                               b.a_batch_y, b.n_valid_y, b.m_valid_y, es, ea, ey, b.status, st,
                               b.n_tiles_y);
@@ -1037,7 +1040,7 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  return launch_gemm<1, PREC>(mA1, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+  return launch_gemm<1, PREC>(mA1, mBV, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch1, b.b_batch1, b.n_valid2, nullptr, es, ea, ey, b.status,
                               st, b.n_tiles_v);
