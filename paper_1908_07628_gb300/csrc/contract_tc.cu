@@ -707,14 +707,26 @@ __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out
   const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d * k1p;
   const float2* src = Sout + (int64_t)d * plane;
   const int P = w * w;
-  for (int p = threadIdx.x; p < k1p / 2; p += blockDim.x) {
-    float2 v = make_float2(0.f, 0.f);
-    if (p < P) {
-      const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
-      v = src[(int64_t)gy * nh + gx];
-    }
+  // consecutive threads take consecutive window pixels (coalesced); the window row and
+  // column of a thread's pixel advance by fixed steps, so no division in the loop
+  const int x0 = wx[s], y0 = wy[s];
+  const int dy = blockDim.x / w, dx = blockDim.x % w;
+  int yy = threadIdx.x / w, xx = threadIdx.x % w;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    int gy = y0 + yy, gx = x0 + xx;
+    if (gy >= nh) gy -= nh;
+    if (gx >= nh) gx -= nh;
+    const float2 v = src[(int64_t)gy * nh + gx];
     put2<PREC>(A1, pstride, rbase + 2 * p, v.x, v.y);
+    xx += dx;
+    yy += dy;
+    if (xx >= w) {
+      xx -= w;
+      ++yy;
+    }
   }
+  for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x)   // K padding
+    put2<PREC>(A1, pstride, rbase + 2 * p, 0.f, 0.f);
 }
 
 // B1[z][plane][2j][2p + c] = H_z[p] Sin[j][p],  B1[z][plane][2j+1] = -i H_z[p] Sin[j][p]
@@ -734,14 +746,27 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
   const float2* Hz = H + ((int64_t)s * h_mul * n_types + z_type[z]) * w * w;
   const float2* src = Sin + (int64_t)j * plane;
   const int P = w * w;
-  for (int p = threadIdx.x; p < k1p / 2; p += blockDim.x) {
-    float2 v = make_float2(0.f, 0.f);
-    if (p < P) {
-      const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
-      v = cmul(Hz[p], src[(int64_t)gy * nh + gx]);
-    }
+  // same incremental pixel walk as the S_out gather
+  const int x0 = wx[s], y0 = wy[s];
+  const int dy = blockDim.x / w, dx = blockDim.x % w;
+  int yy = threadIdx.x / w, xx = threadIdx.x % w;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    int gy = y0 + yy, gx = x0 + xx;
+    if (gy >= nh) gy -= nh;
+    if (gx >= nh) gx -= nh;
+    const float2 v = cmul(Hz[p], src[(int64_t)gy * nh + gx]);
     put2<PREC>(B1, pstride, r0 + 2 * p, v.x, v.y);
     put2<PREC>(B1, pstride, r1 + 2 * p, v.y, -v.x);
+    xx += dx;
+    yy += dy;
+    if (xx >= w) {
+      xx -= w;
+      ++yy;
+    }
+  }
+  for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x) {   // K padding
+    put2<PREC>(B1, pstride, r0 + 2 * p, 0.f, 0.f);
+    put2<PREC>(B1, pstride, r1 + 2 * p, 0.f, 0.f);
   }
 }
 
@@ -820,13 +845,16 @@ __global__ void k_gather_sin_t(const float2* __restrict__ Sin, int nh, int n_in,
   const int P = w * w;
   const int64_t plane = (int64_t)nh * nh;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  int64_t pix = -1;                                         // window pixel of column tx
+  if (p0 + tx < P) {
+    const int p = p0 + tx;
+    const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
+    pix = (int64_t)gy * nh + gx;
+  }
   for (int jj = ty; jj < 32; jj += 8) {
-    const int j = j0 + jj, p = p0 + tx;
+    const int j = j0 + jj;
     float2 v = make_float2(0.f, 0.f);
-    if (j < n_in && p < P) {
-      const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
-      v = Sin[(int64_t)j * plane + (int64_t)gy * nh + gx];
-    }
+    if (j < n_in && pix >= 0) v = Sin[(int64_t)j * plane + pix];
     tile[jj][tx] = v;
   }
   __syncthreads();
