@@ -105,7 +105,10 @@ typedef struct {
   double x0, y0, step_x, step_y;
 } eels_scan;
 
-/* Create a context on CUDA device `device`.  Owns twiddle tables and scratch. */
+/* Create a context on CUDA device `device`.  Owns twiddle tables, options, the grouping
+ * choices of the autotuner and the profiling records.  A context serves one host thread
+ * at a time; threads that compute concurrently each use their own context (as the map
+ * server's workers do).  Different contexts may run concurrently on one device. */
 eels_status eels_create(int device, eels_ctx** out);
 void eels_destroy(eels_ctx* ctx);
 /* Text of the last error raised on this context ("" if none).  Owned by ctx. */

@@ -1,11 +1,30 @@
-// Device helpers shared by the STEM-EELS kernels: complex float2 arithmetic, small
-// in-register DFTs and a register-resident mixed-radix Stockham FFT run by one warp.
+// Helpers shared by the STEM-EELS kernels: complex float2 arithmetic, small
+// in-register DFTs, a register-resident mixed-radix Stockham FFT run by one warp, and a
+// host helper that sets launch attributes once per device.
 #pragma once
+
+#include <atomic>
+#include <cstdint>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace eels {
+
+// Raises a kernel's dynamic shared-memory limit once per device.  `done` holds one bit
+// per device ordinal that already has it; safe to call from several host threads (the
+// map server's workers launch concurrently).
+template <typename K>
+inline cudaError_t smem_attr_once(K* kernel, size_t bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -903,19 +903,12 @@ cudaError_t make_map(CUtensorMap* map, void* base, int k, int rows, int batch, i
 
 template <int PREC>
 cudaError_t set_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0, PREC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_of<0, PREC>());
+  static std::atomic<uint64_t> d0{0}, d1{0}, d2{0};
+  cudaError_t e = smem_attr_once(k_tc_gemm<0, PREC>, smem_of<0, PREC>(), d0);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tc_gemm<1, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_of<1, PREC>());
+  e = smem_attr_once(k_tc_gemm<1, PREC>, smem_of<1, PREC>(), d1);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tc_gemm<2, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_of<2, PREC>());
-  if (e == cudaSuccess) done = true;
-  return e;
+  return smem_attr_once(k_tc_gemm<2, PREC>, smem_of<2, PREC>(), d2);
 }
 
 template <int PREC>
@@ -937,13 +930,16 @@ cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
 }
 
 int sm_count() {
-  static int count[64] = {0};
+  static std::atomic<int> count[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-  if (!count[dev] &&
-      cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    count[dev] = 148;
-  return count[dev];
+  int c = count[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+      c = 148;
+    count[dev].store(c, std::memory_order_relaxed);
+  }
+  return c;
 }
 
 // Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
@@ -957,14 +953,9 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
                         int valid_tiles) {
   if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
   if constexpr (PREC == EELS_TC_TF32 || MODE != 2) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_ws<MODE, PREC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ws::smem<MODE, PREC>());
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_attr_once(k_tc_gemm_ws<MODE, PREC>, ws::smem<MODE, PREC>(), attr);
+    if (e != cudaSuccess) return e;
     const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
     if (tiles <= 0) return cudaSuccess;
     const int grid = std::min(tiles, sm_count());

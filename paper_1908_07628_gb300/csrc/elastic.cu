@@ -207,16 +207,11 @@ cudaError_t cut_fft_detect(float2* X, int n_cut, const uint8_t* mask, int n_det,
                            cudaStream_t s) {
   constexpr int ROWS = RegFFT<M>::ROWS;
   const size_t smem = (size_t)kFftWarps * ROWS * spad_len(M) * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_cut_rows<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_cut_cols_detect<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> rows_attr{0}, cols_attr{0};
+  cudaError_t e0 = smem_attr_once(k_cut_rows<M>, smem, rows_attr);
+  if (e0 != cudaSuccess) return e0;
+  e0 = smem_attr_once(k_cut_cols_detect<M>, smem, cols_attr);
+  if (e0 != cudaSuccess) return e0;
   const int64_t rows = (int64_t)n_cut * M;
   const int64_t per_cta = (int64_t)kFftWarps * ROWS;
   k_cut_rows<M><<<(unsigned)((rows + per_cta - 1) / per_cta), kFftWarps * 32, smem, s>>>(X, rows, tw);
