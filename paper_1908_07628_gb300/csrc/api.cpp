@@ -162,14 +162,12 @@ eels_status twiddles(eels_ctx* ctx, int n, float2** out) {
     *out = it->second;
     return EELS_OK;
   }
-  std::vector<float2> h(n);
-  for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * kPi * (double)k / (double)n;
-    h[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
-  }
+  const int len = eels::twiddle_table_size(n);
+  std::vector<float2> h(len);
+  eels::fill_twiddle_tables(n, h.data());
   float2* d = nullptr;
-  EELS_CK(cudaMalloc((void**)&d, n * sizeof(float2)));
-  EELS_CK(cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  EELS_CK(cudaMalloc((void**)&d, len * sizeof(float2)));
+  EELS_CK(cudaMemcpy(d, h.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
   ctx->tw[n] = d;
   *out = d;
   return EELS_OK;

@@ -101,51 +101,73 @@ __host__ __device__ constexpr int plan_radix_generic(int n, int s) {
 
 // In-register DFT of length R.  INV = false: X_q = sum_n x_n exp(-2 pi i n q / R);
 // INV = true: the + sign.  Unnormalised.
+// `nz`: inputs that may be nonzero (see the input masks below); all by default.
 template <int R, bool INV>
-__device__ __forceinline__ void dft(float2* u);
+__device__ __forceinline__ void dft(float2* u, unsigned nz = ~0u);
 
 template <>
-__device__ __forceinline__ void dft<2, false>(float2* u) { float2 a = u[0]; u[0] = cadd(a, u[1]); u[1] = csub(a, u[1]); }
+__device__ __forceinline__ void dft<2, false>(float2* u, unsigned) { float2 a = u[0]; u[0] = cadd(a, u[1]); u[1] = csub(a, u[1]); }
 template <>
-__device__ __forceinline__ void dft<2, true>(float2* u) { float2 a = u[0]; u[0] = cadd(a, u[1]); u[1] = csub(a, u[1]); }
+__device__ __forceinline__ void dft<2, true>(float2* u, unsigned) { float2 a = u[0]; u[0] = cadd(a, u[1]); u[1] = csub(a, u[1]); }
+
+// Input masks.  The DFTs below take a bit mask `nz` of the inputs that may be nonzero
+// (bit q for input q); inputs outside it must hold zero and the sums and differences
+// with them are skipped.  The masks are compile-time constants once the fully unrolled
+// transforms are inlined, so a pruned butterfly costs nothing at run time.  The first
+// stage of an inverse transform of a band-limited sequence sees half its inputs zero.
+//
+// a + b and a - b where na / nb say whether a / b may be nonzero
+__device__ __forceinline__ float2 cadd_nz(float2 a, float2 b, bool na, bool nb) {
+  return na ? (nb ? cadd(a, b) : a) : (nb ? b : make_float2(0.f, 0.f));
+}
+__device__ __forceinline__ float2 csub_nz(float2 a, float2 b, bool na, bool nb) {
+  return na ? (nb ? csub(a, b) : a) : (nb ? make_float2(-b.x, -b.y) : make_float2(0.f, 0.f));
+}
 
 template <bool INV>
-__device__ __forceinline__ void dft4(float2& u0, float2& u1, float2& u2, float2& u3) {
+__device__ __forceinline__ void dft4(float2& u0, float2& u1, float2& u2, float2& u3,
+                                     unsigned nz = 0xFu) {
   constexpr int S = INV ? 1 : -1;
-  float2 t0 = cadd(u0, u2), t1 = csub(u0, u2);
-  float2 t2 = cadd(u1, u3), t3 = mul_i<S>(csub(u1, u3));
-  u0 = cadd(t0, t2);
-  u2 = csub(t0, t2);
-  u1 = cadd(t1, t3);
-  u3 = csub(t1, t3);
+  const bool n0 = nz & 1u, n1 = nz & 2u, n2 = nz & 4u, n3 = nz & 8u;
+  float2 t0 = cadd_nz(u0, u2, n0, n2), t1 = csub_nz(u0, u2, n0, n2);
+  float2 t2 = cadd_nz(u1, u3, n1, n3), t3 = mul_i<S>(csub_nz(u1, u3, n1, n3));
+  const bool a = n0 || n2, b = n1 || n3;
+  u0 = cadd_nz(t0, t2, a, b);
+  u2 = csub_nz(t0, t2, a, b);
+  u1 = cadd_nz(t1, t3, a, b);
+  u3 = csub_nz(t1, t3, a, b);
 }
 
 template <>
-__device__ __forceinline__ void dft<4, false>(float2* u) { dft4<false>(u[0], u[1], u[2], u[3]); }
+__device__ __forceinline__ void dft<4, false>(float2* u, unsigned nz) { dft4<false>(u[0], u[1], u[2], u[3], nz); }
 template <>
-__device__ __forceinline__ void dft<4, true>(float2* u) { dft4<true>(u[0], u[1], u[2], u[3]); }
+__device__ __forceinline__ void dft<4, true>(float2* u, unsigned nz) { dft4<true>(u[0], u[1], u[2], u[3], nz); }
 
 template <bool INV>
-__device__ __forceinline__ void dft8(float2* u) {
+__device__ __forceinline__ void dft8(float2* u, unsigned nz = 0xFFu) {
   constexpr int S = INV ? 1 : -1;
   constexpr float H = 0.70710678118654752440f;   // 1/sqrt(2)
+  // masks of the even (u0, u2, u4, u6) and odd (u1, u3, u5, u7) inputs
+  const unsigned me = (nz & 1u) | (nz >> 1 & 2u) | (nz >> 2 & 4u) | (nz >> 3 & 8u);
+  const unsigned mo = (nz >> 1 & 1u) | (nz >> 2 & 2u) | (nz >> 3 & 4u) | (nz >> 4 & 8u);
   float2 e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
   float2 o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
-  dft4<INV>(e0, e1, e2, e3);
-  dft4<INV>(o0, o1, o2, o3);
+  dft4<INV>(e0, e1, e2, e3, me);
+  dft4<INV>(o0, o1, o2, o3, mo);
   // o_q *= w8^q, w8 = exp(S 2 pi i / 8)
   o1 = make_float2(H * (o1.x - S * o1.y), H * (o1.y + S * o1.x));
   o2 = mul_i<S>(o2);
   o3 = make_float2(H * (-o3.x - S * o3.y), H * (-o3.y + S * o3.x));
-  u[0] = cadd(e0, o0); u[4] = csub(e0, o0);
-  u[1] = cadd(e1, o1); u[5] = csub(e1, o1);
-  u[2] = cadd(e2, o2); u[6] = csub(e2, o2);
-  u[3] = cadd(e3, o3); u[7] = csub(e3, o3);
+  const bool he = me != 0u, ho = mo != 0u;
+  u[0] = cadd_nz(e0, o0, he, ho); u[4] = csub_nz(e0, o0, he, ho);
+  u[1] = cadd_nz(e1, o1, he, ho); u[5] = csub_nz(e1, o1, he, ho);
+  u[2] = cadd_nz(e2, o2, he, ho); u[6] = csub_nz(e2, o2, he, ho);
+  u[3] = cadd_nz(e3, o3, he, ho); u[7] = csub_nz(e3, o3, he, ho);
 }
 template <>
-__device__ __forceinline__ void dft<8, false>(float2* u) { dft8<false>(u); }
+__device__ __forceinline__ void dft<8, false>(float2* u, unsigned nz) { dft8<false>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<8, true>(float2* u) { dft8<true>(u); }
+__device__ __forceinline__ void dft<8, true>(float2* u, unsigned nz) { dft8<true>(u, nz); }
 
 template <bool INV>
 __device__ __forceinline__ void dft3(float2* u) {
@@ -159,9 +181,9 @@ __device__ __forceinline__ void dft3(float2* u) {
   u[2] = csub(m, r);
 }
 template <>
-__device__ __forceinline__ void dft<3, false>(float2* u) { dft3<false>(u); }
+__device__ __forceinline__ void dft<3, false>(float2* u, unsigned) { dft3<false>(u); }
 template <>
-__device__ __forceinline__ void dft<3, true>(float2* u) { dft3<true>(u); }
+__device__ __forceinline__ void dft<3, true>(float2* u, unsigned) { dft3<true>(u); }
 
 // exp(2 pi i m / 32) components, FP64-rounded to FP32
 __host__ __device__ constexpr float cos32(int m) {
@@ -200,47 +222,73 @@ __device__ __forceinline__ float2 croot(int m, float sg) {
   }
 }
 
+// a exp(+-2 pi i m / R) (+ for INV); quarter turns are exact sign swaps, not products
+template <int R, bool INV>
+__device__ __forceinline__ float2 rotate(float2 a, int m) {
+  constexpr int S = INV ? 1 : -1;
+  if ((4 * m) % R == 0) {
+    const int quarter = (4 * m / R) % 4;
+    return quarter == 0 ? a
+         : quarter == 2 ? make_float2(-a.x, -a.y)
+         : quarter == 1 ? mul_i<S>(a)
+                        : mul_i<-S>(a);
+  }
+  return cmul(a, croot<R>(m, (float)S));
+}
+
 // In-register DFT of length R = R1 R2: n = R2 n1 + n2, k = k1 + R1 k2;
 // DFT_R1 over n1, twiddle exp(+-2 pi i n2 k1 / R), DFT_R2 over n2.
 template <int R1, int R2, bool INV>
-__device__ __forceinline__ void dft_composite(float2* x) {
+__device__ __forceinline__ void dft_composite(float2* x, unsigned nz) {
   constexpr int R = R1 * R2;
-  constexpr float SG = INV ? 1.f : -1.f;
   float2 y[R];
+  unsigned live = 0u;   // n2 whose length-R1 transform has a nonzero input
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) {
     float2 t[R1];
+    unsigned sub = 0u;
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[R2 * n1 + n2];
-    dft<R1, INV>(t);
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) {
-      const int m = (n2 * k1) % R;
-      y[n2 * R1 + k1] = m == 0 ? t[k1] : cmul(t[k1], croot<R>(m, SG));
+    for (int n1 = 0; n1 < R1; ++n1) {
+      t[n1] = x[R2 * n1 + n2];
+      if (nz >> (R2 * n1 + n2) & 1u) sub |= 1u << n1;
     }
+    if (sub) live |= 1u << n2;
+    dft<R1, INV>(t, sub);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) y[n2 * R1 + k1] = rotate<R, INV>(t[k1], (n2 * k1) % R);
   }
 #pragma unroll
   for (int k1 = 0; k1 < R1; ++k1) {
     float2 t[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
-    dft<R2, INV>(t);
+    dft<R2, INV>(t, live);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
   }
 }
 template <>
-__device__ __forceinline__ void dft<16, false>(float2* u) { dft_composite<4, 4, false>(u); }
+__device__ __forceinline__ void dft<16, false>(float2* u, unsigned nz) { dft_composite<4, 4, false>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<16, true>(float2* u) { dft_composite<4, 4, true>(u); }
+__device__ __forceinline__ void dft<16, true>(float2* u, unsigned nz) { dft_composite<4, 4, true>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<24, false>(float2* u) { dft_composite<8, 3, false>(u); }
+__device__ __forceinline__ void dft<24, false>(float2* u, unsigned nz) { dft_composite<8, 3, false>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<24, true>(float2* u) { dft_composite<8, 3, true>(u); }
+__device__ __forceinline__ void dft<24, true>(float2* u, unsigned nz) { dft_composite<8, 3, true>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<32, false>(float2* u) { dft_composite<8, 4, false>(u); }
+__device__ __forceinline__ void dft<32, false>(float2* u, unsigned nz) { dft_composite<8, 4, false>(u, nz); }
 template <>
-__device__ __forceinline__ void dft<32, true>(float2* u) { dft_composite<8, 4, true>(u); }
+__device__ __forceinline__ void dft<32, true>(float2* u, unsigned nz) { dft_composite<8, 4, true>(u, nz); }
+
+// First-stage input mask of an inverse transform whose input is band-limited to
+// |frequency| < N/4: for radix R (a multiple of 4) input q holds frequency b + q N/R with
+// b < N/R, inside the band iff q < R/4 or q >= 3R/4.
+__host__ __device__ constexpr unsigned band_mask(int r) {
+  unsigned m = 0u;
+  for (int q = 0; q < r; ++q)
+    if (4 * q < r || 4 * q >= 3 * r) m |= 1u << q;
+  return m;
+}
 
 // ---------------------------------------------------------------------------
 // Register-resident warp FFT.
@@ -297,6 +345,15 @@ __host__ __device__ constexpr int pad_of() {
   return plan2_radix(N, 0) > 0 ? (REV ? plan_radix(N, plan_len(N) - 1) : plan_radix(N, 0)) : 8;
 }
 
+// Twiddle tables.  A table for length N holds 3N float2 values:
+//   [0, N)    exp(-2 pi i n / N);
+//   [N, 2N)   for a two-stage plan (radices R0, R1; R0 R1 = N), the second stage's
+//             factors exp(-2 pi i q k / N) at N + q R0 + k (q < R1, k < R0);
+//   [2N, 3N)  the same for the reversed plan (radices R1, R0), at 2N + q R1 + k.
+// The last two ranges are unused (zero) for plans of more than two stages.
+__host__ __device__ constexpr int twiddle_table_offset(int n, bool rev) { return rev ? 2 * n : n; }
+__host__ __device__ constexpr int twiddle_table_len(int n) { return 3 * n; }
+
 // Twiddles exp(-+2 pi i q k s / N) for q = 1..R-1 of one butterfly: one or two table
 // loads and products (at most six roundings) instead of R - 1 loads.
 template <int N, int R, bool INV>
@@ -337,7 +394,8 @@ __device__ __forceinline__ void twiddles(float2* w, int ks, const float2* __rest
 // sbuf + r * ld in the warp's shared buffer.
 template <int N, bool INV, bool REV, int S>
 __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
-                                              const float2* __restrict__ tw, int lane) {
+                                              const float2* __restrict__ tw, int lane,
+                                              unsigned nz) {
   using PL = Plan<N, REV>;
   constexpr int ROWS = PL::ROWS;
   constexpr int PAD = pad_of<N, REV>();
@@ -347,14 +405,23 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
     const int u = lane + 32 * t;
     if ((ROWS * NB) % 32 == 0 || u < ROWS * NB) {
       const int b = u % NB;
-      if constexpr (P > 1) {
+      if constexpr (P > 1 && PL::NS == 2) {
+        // second stage of a two-stage plan (P R = N): one table load per twiddle
+        // exp(-2 pi i q k / N), stored at q P + k so that a warp reads a contiguous run
+        const float2* __restrict__ tab = tw + twiddle_table_offset(N, REV) + b % P;
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          const float2 w = __ldg(tab + q * P);
+          v[t * R + q] = INV ? cmulc(v[t * R + q], w) : cmul(v[t * R + q], w);
+        }
+      } else if constexpr (P > 1) {
         const int k = b % P;
         float2 w[R];
         twiddles<N, R, INV>(w, k * (N / (P * R)), tw);
 #pragma unroll
         for (int q = 1; q < R; ++q) v[t * R + q] = cmul(v[t * R + q], w[q]);
       }
-      dft<R, INV>(v + t * R);
+      dft<R, INV>(v + t * R, S == 0 ? nz : ~0u);
     }
   }
   if constexpr (S + 1 < PL::NS) {
@@ -383,17 +450,19 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
       }
     }
     __syncwarp();
-    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, ld, tw, lane);
+    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, ld, tw, lane, ~0u);
   }
 }
 
 // Transform the ROWS warp-held sequences.  On entry slot u of v holds
 // x_{u/NB0}[u%NB0 + q N/R0] (R0 = first radix), on exit X in the same form for the
-// last radix.  tw[n] = exp(-2 pi i n/N).
+// last radix.  `tw` is a table built by fill_twiddle_tables for this N.  `nz0` masks
+// the first stage's inputs q that may be nonzero (band_mask for a band-limited input).
 template <int N, bool INV, bool REV>
 __device__ __forceinline__ void reg_fft(float2* v, float2* sbuf, int ld,
-                                        const float2* __restrict__ tw, int lane) {
-  reg_fft_stage<N, INV, REV, 0>(v, sbuf, ld, tw, lane);
+                                        const float2* __restrict__ tw, int lane,
+                                        unsigned nz0 = ~0u) {
+  reg_fft_stage<N, INV, REV, 0>(v, sbuf, ld, tw, lane, nz0);
 }
 
 }  // namespace eels

@@ -10,6 +10,12 @@ namespace eels {
 // True if the multislice kernels are compiled for grid side n.
 bool grid_supported(int n);
 
+// Number of float2 values in the twiddle table of a length-n transform, and the host
+// routine that fills one (exp(-2 pi i k / n) and the second-stage factor tables of the
+// two-stage plans, each rounded from FP64).  Every FFT kernel takes such a table.
+int twiddle_table_size(int n);
+void fill_twiddle_tables(int n, float2* h);
+
 // t[i][y][x] = exp(i sigma v[i][y][x]) with the phase in FP64 (Eqs. 3-4).
 cudaError_t launch_transmission(const float* v, double sigma, float2* t, int64_t count,
                                 cudaStream_t s);

@@ -16,6 +16,8 @@
 // Scale convention: W holds the true row spectrum; the row pass produces N times
 // the true real-space wave and N times the true row spectrum, and the propagator
 // table carries the 1/N^2 that restores W after the column pass.
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -63,7 +65,7 @@ __device__ __forceinline__ void row_pass_body(const float2* __restrict__ W, floa
       }
     }
   }
-  reg_fft<N, true, true>(v, sbuf, LDR, tw, lane);
+  reg_fft<N, true, true>(v, sbuf, LDR, tw, lane, band_mask(PI::R(0)));
 
   // real space: slot u holds N psi(x = u%NBL + q N/RL, y0 + u/NBL)
   {
@@ -215,7 +217,7 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
       }
     }
     __syncwarp();
-    reg_fft<N, true, true>(v, sbuf, LD, tw, lane);
+    reg_fft<N, true, true>(v, sbuf, LD, tw, lane, band_mask(PI::R(0)));
     {
       constexpr int RL = PI::R(PI::NS - 1), NBL = N / RL, PERL = PI::per(PI::NS - 1);
 #pragma unroll
@@ -447,6 +449,25 @@ bool grid_supported(int n) {
   EELS_FOR_EACH_N(EELS_CASE)
 #undef EELS_CASE
   return false;
+}
+
+int twiddle_table_size(int n) { return twiddle_table_len(n); }
+
+void fill_twiddle_tables(int n, float2* h) {
+  auto root = [n](int64_t e) {
+    const double a = 2.0 * 3.14159265358979323846 * (double)(e % n) / (double)n;
+    return make_float2((float)std::cos(a), (float)-std::sin(a));
+  };
+  for (int k = 0; k < n; ++k) h[k] = root(k);
+  for (int k = n; k < twiddle_table_len(n); ++k) h[k] = make_float2(0.f, 0.f);
+  if (plan_len(n) != 2) return;
+  for (int rev = 0; rev < 2; ++rev) {
+    // stage 1 of the plan: radix r1 after a first stage of radix r0 (r0 r1 = n)
+    const int r0 = plan_radix(n, rev ? 1 : 0), r1 = plan_radix(n, rev ? 0 : 1);
+    float2* t = h + twiddle_table_offset(n, rev != 0);
+    for (int q = 0; q < r1; ++q)
+      for (int k = 0; k < r0; ++k) t[q * r0 + k] = root((int64_t)q * k);
+  }
 }
 
 cudaError_t launch_row_pass(int n, int n_waves, const float2* W, float2* Phi, const float2* t,

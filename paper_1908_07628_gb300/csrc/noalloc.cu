@@ -118,7 +118,7 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
   // carve the static array: twiddles | propagator | one transmission slice |
   // one potential slice | beam lists | W | Phi (waves processed in chunks)
   size_t off = 0;
-  const size_t o_tw = off;   off = align256(off + sizeof(float2) * n);
+  const size_t o_tw = off;   off = align256(off + sizeof(float2) * eels::twiddle_table_size(n));
   const size_t o_p = off;    off = align256(off + sizeof(float2) * plane);
   const size_t o_t = off;    off = align256(off + sizeof(float2) * (size_t)n * n);
   const size_t o_v = off;    off = align256(off + sizeof(float) * (size_t)n * n);
@@ -157,11 +157,8 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
   float2* Phi = reinterpret_cast<float2*>(base + o_phi);
 
   // host-computed tables, copied into the static array
-  std::vector<float2> htw(n), hamp(n_in, make_float2(1.f, 0.f));
-  for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * 3.14159265358979323846 * (double)k / (double)n;
-    htw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
-  }
+  std::vector<float2> htw(eels::twiddle_table_size(n)), hamp(n_in, make_float2(1.f, 0.f));
+  eels::fill_twiddle_tables(n, htw.data());
 #define EELS_SCK(call)                                      \
   do {                                                      \
     cudaError_t e_ = (call);                                \
@@ -170,7 +167,8 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
       return EELS_ERR_CUDA;                                 \
     }                                                       \
   } while (0)
-  EELS_SCK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, st));
+  EELS_SCK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * htw.size(), cudaMemcpyHostToDevice,
+                           st));
   EELS_SCK(cudaMemcpyAsync(dpx, px.data(), sizeof(int) * n_in, cudaMemcpyHostToDevice, st));
   EELS_SCK(cudaMemcpyAsync(dpy, py.data(), sizeof(int) * n_in, cudaMemcpyHostToDevice, st));
   EELS_SCK(cudaMemcpyAsync(damp, hamp.data(), sizeof(float2) * n_in, cudaMemcpyHostToDevice, st));
