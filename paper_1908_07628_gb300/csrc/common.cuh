@@ -392,7 +392,7 @@ __device__ __forceinline__ void twiddles(float2* w, int ks, const float2* __rest
 // Butterfly slot u = lane + 32 t of a stage with NB butterflies per sequence
 // belongs to sequence u / NB, butterfly u % NB.  Sequence r lives at
 // sbuf + r * ld in the warp's shared buffer.
-template <int N, bool INV, bool REV, int S>
+template <int N, bool INV, bool REV, int S, bool TAB>
 __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
                                               const float2* __restrict__ tw, int lane,
                                               unsigned nz) {
@@ -405,7 +405,7 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
     const int u = lane + 32 * t;
     if ((ROWS * NB) % 32 == 0 || u < ROWS * NB) {
       const int b = u % NB;
-      if constexpr (P > 1 && PL::NS == 2) {
+      if constexpr (TAB && P > 1 && PL::NS == 2) {
         // second stage of a two-stage plan (P R = N): one table load per twiddle
         // exp(-2 pi i q k / N), stored at q P + k so that a warp reads a contiguous run
         const float2* __restrict__ tab = tw + twiddle_table_offset(N, REV) + b % P;
@@ -450,7 +450,7 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
       }
     }
     __syncwarp();
-    reg_fft_stage<N, INV, REV, S + 1>(v, sbuf, ld, tw, lane, ~0u);
+    reg_fft_stage<N, INV, REV, S + 1, TAB>(v, sbuf, ld, tw, lane, ~0u);
   }
 }
 
@@ -458,11 +458,24 @@ __device__ __forceinline__ void reg_fft_stage(float2* v, float2* sbuf, int ld,
 // x_{u/NB0}[u%NB0 + q N/R0] (R0 = first radix), on exit X in the same form for the
 // last radix.  `tw` is a table built by fill_twiddle_tables for this N.  `nz0` masks
 // the first stage's inputs q that may be nonzero (band_mask for a band-limited input).
-template <int N, bool INV, bool REV>
+// TAB: a two-stage plan reads its second-stage twiddles from the table (one L1 load
+// each) instead of forming them by products from two loads (about one complex product
+// each); the first suits kernels bound by arithmetic issue, the second kernels bound by
+// L1 / shared-memory wavefronts.
+template <int N, bool INV, bool REV, bool TAB = true>
 __device__ __forceinline__ void reg_fft(float2* v, float2* sbuf, int ld,
                                         const float2* __restrict__ tw, int lane,
                                         unsigned nz0 = ~0u) {
-  reg_fft_stage<N, INV, REV, 0>(v, sbuf, ld, tw, lane, nz0);
+  reg_fft_stage<N, INV, REV, 0, TAB>(v, sbuf, ld, tw, lane, nz0);
+}
+
+// Table twiddles for a transform in a wavefront-bound kernel: only where a warp's reads
+// of one factor index take a single wavefront (at most 16 distinct entries) or serve
+// two sequences at once.
+template <int N, bool REV>
+__host__ __device__ constexpr bool table_twiddles_cheap() {
+  using PL = Plan<N, REV>;
+  return PL::NS == 2 && (PL::R(0) <= 16 || PL::per(1) > 1);
 }
 
 }  // namespace eels

@@ -694,6 +694,39 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
   if (!ok && status) atomicExch(status, 1);
 }
 
+// Window gathers: consecutive threads take consecutive window pixels (coalesced).  A
+// thread's pixels p0, p0 + blockDim.x, ... are visited by an incremental walk (the window
+// row and column advance by fixed steps, no division), and each batch of kGatherBatch
+// loads is issued before any of its stores so that the loads overlap.
+constexpr int kGatherBatch = 4;
+
+struct WindowWalk {
+  int x0, y0, w, nh, dx, dy, xx, yy;
+  __device__ WindowWalk(int x0_, int y0_, int w_, int nh_)
+      : x0(x0_), y0(y0_), w(w_), nh(nh_), dx(blockDim.x % w_), dy(blockDim.x / w_),
+        xx(threadIdx.x % w_), yy(threadIdx.x / w_) {}
+  // v[u] = plane[pixel p0 + u blockDim.x of the periodic window] for the pixels below P
+  __device__ __forceinline__ void load(const float2* __restrict__ plane, int p0, int P,
+                                       float2* v) {
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      v[u] = make_float2(0.f, 0.f);
+      if (p0 + u * (int)blockDim.x < P) {
+        int gy = y0 + yy, gx = x0 + xx;
+        if (gy >= nh) gy -= nh;
+        if (gx >= nh) gx -= nh;
+        v[u] = plane[(int64_t)gy * nh + gx];
+        xx += dx;
+        yy += dy;
+        if (xx >= w) {
+          xx -= w;
+          ++yy;
+        }
+      }
+    }
+  }
+};
+
 // A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]]
 template <int PREC>
 __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out, int w,
@@ -707,22 +740,14 @@ __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out
   const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d * k1p;
   const float2* src = Sout + (int64_t)d * plane;
   const int P = w * w;
-  // consecutive threads take consecutive window pixels (coalesced); the window row and
-  // column of a thread's pixel advance by fixed steps, so no division in the loop
-  const int x0 = wx[s], y0 = wy[s];
-  const int dy = blockDim.x / w, dx = blockDim.x % w;
-  int yy = threadIdx.x / w, xx = threadIdx.x % w;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    int gy = y0 + yy, gx = x0 + xx;
-    if (gy >= nh) gy -= nh;
-    if (gx >= nh) gx -= nh;
-    const float2 v = src[(int64_t)gy * nh + gx];
-    put2<PREC>(A1, pstride, rbase + 2 * p, v.x, v.y);
-    xx += dx;
-    yy += dy;
-    if (xx >= w) {
-      xx -= w;
-      ++yy;
+  WindowWalk walk(wx[s], wy[s], w, nh);
+  for (int p0 = threadIdx.x; p0 < P; p0 += kGatherBatch * blockDim.x) {
+    float2 v[kGatherBatch];
+    walk.load(src, p0, P, v);
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int p = p0 + u * blockDim.x;
+      if (p < P) put2<PREC>(A1, pstride, rbase + 2 * p, v[u].x, v[u].y);
     }
   }
   for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x)   // K padding
@@ -746,22 +771,18 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
   const float2* Hz = H + ((int64_t)s * h_mul * n_types + z_type[z]) * w * w;
   const float2* src = Sin + (int64_t)j * plane;
   const int P = w * w;
-  // same incremental pixel walk as the S_out gather
-  const int x0 = wx[s], y0 = wy[s];
-  const int dy = blockDim.x / w, dx = blockDim.x % w;
-  int yy = threadIdx.x / w, xx = threadIdx.x % w;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    int gy = y0 + yy, gx = x0 + xx;
-    if (gy >= nh) gy -= nh;
-    if (gx >= nh) gx -= nh;
-    const float2 v = cmul(Hz[p], src[(int64_t)gy * nh + gx]);
-    put2<PREC>(B1, pstride, r0 + 2 * p, v.x, v.y);
-    put2<PREC>(B1, pstride, r1 + 2 * p, v.y, -v.x);
-    xx += dx;
-    yy += dy;
-    if (xx >= w) {
-      xx -= w;
-      ++yy;
+  WindowWalk walk(wx[s], wy[s], w, nh);
+  for (int p0 = threadIdx.x; p0 < P; p0 += kGatherBatch * blockDim.x) {
+    float2 v[kGatherBatch];
+    walk.load(src, p0, P, v);
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int p = p0 + u * blockDim.x;
+      if (p < P) {
+        const float2 h = cmul(Hz[p], v[u]);
+        put2<PREC>(B1, pstride, r0 + 2 * p, h.x, h.y);
+        put2<PREC>(B1, pstride, r1 + 2 * p, h.y, -h.x);
+      }
     }
   }
   for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x) {   // K padding
@@ -851,12 +872,15 @@ __global__ void k_gather_sin_t(const float2* __restrict__ Sin, int nh, int n_in,
     const int gy = (wy[s] + p / w) % nh, gx = (wx[s] + p % w) % nh;
     pix = (int64_t)gy * nh + gx;
   }
-  for (int jj = ty; jj < 32; jj += 8) {
-    const int j = j0 + jj;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < n_in && pix >= 0) v = Sin[(int64_t)j * plane + pix];
-    tile[jj][tx] = v;
+  // the four loads of a thread in flight together
+  float2 got[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = j0 + ty + 8 * u;
+    got[u] = (j < n_in && pix >= 0) ? Sin[(int64_t)j * plane + pix] : make_float2(0.f, 0.f);
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) tile[ty + 8 * u][tx] = got[u];
   __syncthreads();
   const int64_t pstride = (int64_t)k1p * k2p;
   for (int pp = ty; pp < 32; pp += 8) {

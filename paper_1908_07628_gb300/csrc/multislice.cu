@@ -195,7 +195,8 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
     }
   }
   __syncwarp();
-  reg_fft<N, false, false>(v, sbuf, LD, tw, lane);
+  // the column pass is bound by wavefronts as much as by arithmetic
+  reg_fft<N, false, false, table_twiddles_cheap<N, false>()>(v, sbuf, LD, tw, lane);
   // y-spectrum: slot u holds ky = u%NBF + q N/RF of column kx0 + warp*ROWS + u/NBF
   constexpr int RF = PF::R(PF::NS - 1), NBF = N / RF, PERF = PF::per(PF::NS - 1);
   if (mode == 0) {
@@ -217,7 +218,8 @@ k_col_pass(const float2* __restrict__ Phi, float2* __restrict__ W,
       }
     }
     __syncwarp();
-    reg_fft<N, true, true>(v, sbuf, LD, tw, lane, band_mask(PI::R(0)));
+    reg_fft<N, true, true, table_twiddles_cheap<N, true>()>(v, sbuf, LD, tw, lane,
+                                                           band_mask(PI::R(0)));
     {
       constexpr int RL = PI::R(PI::NS - 1), NBL = N / RL, PERL = PI::per(PI::NS - 1);
 #pragma unroll
