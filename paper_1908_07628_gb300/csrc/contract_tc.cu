@@ -705,17 +705,16 @@ struct WindowWalk {
   __device__ WindowWalk(int x0_, int y0_, int w_, int nh_)
       : x0(x0_), y0(y0_), w(w_), nh(nh_), dx(blockDim.x % w_), dy(blockDim.x / w_),
         xx(threadIdx.x % w_), yy(threadIdx.x / w_) {}
-  // v[u] = plane[pixel p0 + u blockDim.x of the periodic window] for the pixels below P
-  __device__ __forceinline__ void load(const float2* __restrict__ plane, int p0, int P,
-                                       float2* v) {
+  // off[u] = plane offset of pixel p0 + u blockDim.x of the periodic window, -1 past P
+  __device__ __forceinline__ void offsets(int p0, int P, int* off) {
 #pragma unroll
     for (int u = 0; u < kGatherBatch; ++u) {
-      v[u] = make_float2(0.f, 0.f);
+      off[u] = -1;
       if (p0 + u * (int)blockDim.x < P) {
         int gy = y0 + yy, gx = x0 + xx;
         if (gy >= nh) gy -= nh;
         if (gx >= nh) gx -= nh;
-        v[u] = plane[(int64_t)gy * nh + gx];
+        off[u] = gy * nh + gx;
         xx += dx;
         yy += dy;
         if (xx >= w) {
@@ -725,33 +724,58 @@ struct WindowWalk {
       }
     }
   }
+  // v[u] = plane[pixel p0 + u blockDim.x of the window], zero past P
+  __device__ __forceinline__ void load(const float2* __restrict__ plane, int p0, int P,
+                                       float2* v) {
+    int off[kGatherBatch];
+    offsets(p0, P, off);
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u)
+      v[u] = off[u] >= 0 ? plane[off[u]] : make_float2(0.f, 0.f);
+  }
 };
 
-// A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]]
+// Beams of S_out per block of the S_out gather, and probe rows per block of the
+// probe-row gather: enough loads per thread to cover the memory latency.
+constexpr int kSoutBeams = 4;
+constexpr int kArowRows = 4;
+
+// A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]];
+// a block takes kSoutBeams beams d of one site.
 template <int PREC>
 __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out, int w,
                               const int* __restrict__ slot_site, const int* __restrict__ wx,
                               const int* __restrict__ wy, void* __restrict__ A1, int k1p) {
   constexpr int PL = Prec<PREC>::PLANES;
-  const int d = blockIdx.x, slot = blockIdx.y;
+  const int d0 = blockIdx.x * kSoutBeams, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int64_t plane = (int64_t)nh * nh;
   const int64_t pstride = (int64_t)n_out * k1p;
-  const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d * k1p;
-  const float2* src = Sout + (int64_t)d * plane;
+  const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d0 * k1p;
+  const float2* src = Sout + (int64_t)d0 * plane;
+  const int nb = min(kSoutBeams, n_out - d0);
   const int P = w * w;
   WindowWalk walk(wx[s], wy[s], w, nh);
   for (int p0 = threadIdx.x; p0 < P; p0 += kGatherBatch * blockDim.x) {
-    float2 v[kGatherBatch];
-    walk.load(src, p0, P, v);
+    int off[kGatherBatch];
+    walk.offsets(p0, P, off);
+    float2 v[kSoutBeams][kGatherBatch];
 #pragma unroll
-    for (int u = 0; u < kGatherBatch; ++u) {
-      const int p = p0 + u * blockDim.x;
-      if (p < P) put2<PREC>(A1, pstride, rbase + 2 * p, v[u].x, v[u].y);
-    }
+    for (int b = 0; b < kSoutBeams; ++b)
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u)
+        v[b][u] = (b < nb && off[u] >= 0) ? src[b * plane + off[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < kSoutBeams; ++b)
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u)
+        if (b < nb && off[u] >= 0)
+          put2<PREC>(A1, pstride, rbase + (int64_t)b * k1p + 2 * (p0 + u * (int)blockDim.x),
+                     v[b][u].x, v[b][u].y);
   }
-  for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x)   // K padding
-    put2<PREC>(A1, pstride, rbase + 2 * p, 0.f, 0.f);
+  for (int b = 0; b < nb; ++b)
+    for (int p = P + threadIdx.x; p < k1p / 2; p += blockDim.x)   // K padding
+      put2<PREC>(A1, pstride, rbase + (int64_t)b * k1p + 2 * p, 0.f, 0.f);
 }
 
 // B1[z][plane][2j][2p + c] = H_z[p] Sin[j][p],  B1[z][plane][2j+1] = -i H_z[p] Sin[j][p]
@@ -823,7 +847,8 @@ __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __r
   }
 }
 
-// AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = axT[ix(r)][j] ayT[iy(r)][j]
+// AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = axT[ix(r)][j] ayT[iy(r)][j];
+// a block takes kArowRows rows r of one site.
 template <int PREC>
 __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __restrict__ ayT,
                                int n_in, const int* __restrict__ slot_site,
@@ -832,23 +857,34 @@ __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __r
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
                                int nr_cap, void* __restrict__ AY, int k2p) {
   constexpr int PL = Prec<PREC>::PLANES;
-  const int r = blockIdx.x, slot = blockIdx.y;
+  const int rb = blockIdx.x * kArowRows, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
-  if (r >= (nr + BM - 1) / BM * BM) return;   // rows of M tiles GEMM-Y skips
+  const int r_end = min((nr + BM - 1) / BM * BM, nr_cap);   // rows of M tiles GEMM-Y reads
+  if (rb >= r_end) return;
   const int64_t pstride = (int64_t)nr_cap * k2p;
-  const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)r * k2p;
-  int ix = 0, iy = 0;
-  if (r < nr) {
-    ix = xlist[xoff[s] + r % nx];
-    iy = ylist[yoff[s] + r / nx];
+  const float2* axr[kArowRows];
+  const float2* ayr[kArowRows];
+  bool live[kArowRows];
+#pragma unroll
+  for (int i = 0; i < kArowRows; ++i) {
+    const int r = rb + i;
+    live[i] = r < nr;
+    const int ix = live[i] ? xlist[xoff[s] + r % nx] : 0;
+    const int iy = live[i] ? ylist[yoff[s] + r / nx] : 0;
+    axr[i] = axT + (int64_t)ix * n_in;
+    ayr[i] = ayT + (int64_t)iy * n_in;
   }
-  const float2* axr = axT + (int64_t)ix * n_in;
-  const float2* ayr = ayT + (int64_t)iy * n_in;
   for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
-    float2 a = make_float2(0.f, 0.f);
-    if (r < nr && j < n_in) a = cmul(axr[j], ayr[j]);
-    put2<PREC>(AY, pstride, r0 + 2 * j, a.x, a.y);
+    float2 a[kArowRows];
+#pragma unroll
+    for (int i = 0; i < kArowRows; ++i)
+      a[i] = (live[i] && j < n_in) ? cmul(axr[i][j], ayr[i][j]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kArowRows; ++i)
+      if (rb + i < r_end)
+        put2<PREC>(AY, pstride, (int64_t)slot * PL * pstride + (int64_t)(rb + i) * k2p + 2 * j,
+                   a[i].x, a[i].y);
   }
 }
 
@@ -939,9 +975,8 @@ template <int PREC>
 cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
   const int nz = b.n_sites * b.n_types;
   cudaError_t e;
-  k_gather_sout<PREC><<<dim3(b.n_out, b.n_sites), 256, 0, st>>>(b.Sout, b.nh, b.n_out, b.w,
-                                                                 b.slot_site, b.wx, b.wy, b.A1,
-                                                                 b.k1p);
+  k_gather_sout<PREC><<<dim3((b.n_out + kSoutBeams - 1) / kSoutBeams, b.n_sites), 256, 0, st>>>(
+      b.Sout, b.nh, b.n_out, b.w, b.slot_site, b.wx, b.wy, b.A1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_sin_h<PREC><<<dim3(b.n_in, nz), 256, 0, st>>>(b.Sin, b.nh, b.n_in, b.w, b.z_site,
                                                           b.z_type, b.H, b.n_types, b.h_mul, b.wx,
@@ -1035,11 +1070,10 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
 template <int PREC>
 cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
-  k_gather_sout<PREC><<<dim3(b.n_out, b.n_sites), 256, 0, st>>>(b.Sout, b.nh, b.n_out, b.w,
-                                                                 b.slot_site, b.wx, b.wy, b.A1,
-                                                                 b.k1p);
+  k_gather_sout<PREC><<<dim3((b.n_out + kSoutBeams - 1) / kSoutBeams, b.n_sites), 256, 0, st>>>(
+      b.Sout, b.nh, b.n_out, b.w, b.slot_site, b.wx, b.wy, b.A1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_gather_arows<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
+  k_gather_arows<PREC><<<dim3((b.nr_cap + kArowRows - 1) / kArowRows, b.n_sites), 256, 0, st>>>(
       b.axT, b.ayT, b.n_in, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
       b.nr_cap, b.AY, b.k2p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
