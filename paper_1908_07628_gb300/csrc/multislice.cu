@@ -304,26 +304,40 @@ __global__ void k_propagator_table(float2* __restrict__ ptab, int n, double cell
   }
 }
 
+// One block writes kInitRows rows of one wave as float4 pairs of row-spectrum values
+// (N/2 is even, so every row starts on a 16-byte boundary); only the thread holding
+// column box(px) computes a nonzero value.
+constexpr int kInitRows = 16;
+
 __global__ void k_init_plane_waves(float2* __restrict__ W, int n, const int* __restrict__ px,
                                    const int* __restrict__ py, const float2* __restrict__ amp,
                                    const float2* __restrict__ tw) {
-  const int nh = n / 2;
+  const int nh = n / 2, npair = nh / 2;
   const int64_t wave = blockIdx.y;
   const int col = px[wave] >= 0 ? px[wave] : px[wave] + nh;
-  const int64_t per = (int64_t)n * nh;
-  float2* dst = W + wave * per;
   const float2 a = amp[wave];
   const int q = py[wave];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(i / nh), k = (int)(i % nh);
-    float2 v = make_float2(0.f, 0.f);
-    if (k == col) {
-      int m = (int)(((int64_t)q * y) % n);
-      if (m < 0) m += n;
-      v = cmul(a, cconj(tw[m]));   // exp(+2 pi i q y / N)
+  float4* base = reinterpret_cast<float4*>(W + wave * (int64_t)n * nh);
+  const int y0 = blockIdx.x * kInitRows;
+  for (int r = 0; r < kInitRows && y0 + r < n; ++r) {
+    const int y = y0 + r;
+    float4* row = base + (int64_t)y * npair;
+    for (int k2 = threadIdx.x; k2 < npair; k2 += blockDim.x) {
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k2 == (col >> 1)) {
+        int m = (int)(((int64_t)q * y) % n);
+        if (m < 0) m += n;
+        const float2 v = cmul(a, cconj(tw[m]));   // exp(+2 pi i q y / N)
+        if (col & 1) {
+          o.z = v.x;
+          o.w = v.y;
+        } else {
+          o.x = v.x;
+          o.y = v.y;
+        }
+      }
+      row[k2] = o;
     }
-    dst[i] = v;
   }
 }
 
@@ -510,9 +524,8 @@ cudaError_t launch_propagator_table(float2* ptab, int n, double cell, double lam
 cudaError_t launch_init_plane_waves(float2* W, int n, int n_waves, const int* px, const int* py,
                                     const float2* amp, const float2* tw, cudaStream_t s) {
   if (n_waves <= 0) return cudaSuccess;
-  const int64_t per = (int64_t)n * (n / 2);
-  dim3 grid((unsigned)((per + 255) / 256), n_waves);
-  k_init_plane_waves<<<grid, 256, 0, s>>>(W, n, px, py, amp, tw);
+  dim3 grid((unsigned)((n + kInitRows - 1) / kInitRows), n_waves);
+  k_init_plane_waves<<<grid, 128, 0, s>>>(W, n, px, py, amp, tw);
   return cudaGetLastError();
 }
 
