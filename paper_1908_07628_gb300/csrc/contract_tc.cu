@@ -17,10 +17,8 @@
 //           planes); each product is lo*hi + hi*lo + hi*hi with kind::f16 MMAs into
 //           the same FP32 accumulator (the lo*lo term is below FP32 resolution).
 // Operands are gathered into K-padded buffers [batch][plane][rows][K] and streamed
-// by TMA (128-byte swizzle) through an mbarrier pipeline.  The GEMMs run a persistent,
-// warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws); GEMM-Y
-// in BF16 hi + lo runs one 128 x 256 tile per CTA (k_tc_gemm): warp 0 lane 0 issues TMA,
-// warp 1 lane 0 issues MMA, all four warps drain TMEM in the epilogue.
+// by TMA (128-byte swizzle) through an mbarrier pipeline.  Every GEMM runs one persistent,
+// warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws).
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -44,7 +42,6 @@ struct Prec<EELS_TC_TF32> {
   using T = float;
   static constexpr int BK = 32;         // 128 bytes of K per row
   static constexpr int PLANES = 1;
-  static constexpr int STAGES = 4;
   static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   static constexpr uint32_t IDESC = tc::idesc_tf32(BM, BN);
 };
@@ -53,7 +50,6 @@ struct Prec<EELS_TC_BF16X3> {
   using T = __nv_bfloat16;
   static constexpr int BK = 64;
   static constexpr int PLANES = 2;      // hi, lo
-  static constexpr int STAGES = 2;
   static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   static constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
 };
@@ -65,17 +61,6 @@ struct Tile {
   static constexpr int B_BYTES = BN * P::BK * (int)sizeof(typename P::T);
   static constexpr int STAGE_BYTES = P::PLANES * (A_BYTES + B_BYTES);
 };
-
-// Pipeline depth of a GEMM mode.  TF32 runs two stages: two CTAs then share an SM
-// and one's epilogue overlaps the other's main loop.
-template <int MODE, int PREC>
-__host__ __device__ constexpr int stages_of() {
-  return PREC == EELS_TC_TF32 ? 2 : Prec<PREC>::STAGES;
-}
-template <int MODE, int PREC>
-__host__ __device__ constexpr size_t smem_of() {
-  return (size_t)stages_of<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + 1024 + 256;
-}
 
 // store the pair (a, b) at element e of a row, in every plane of the precision
 template <int PREC>
@@ -91,6 +76,16 @@ __device__ __forceinline__ void put2(void* base, int64_t plane_stride, int64_t e
     reinterpret_cast<__nv_bfloat162*>(p + e)[0] = __halves2bfloat162(ah, bh);
     reinterpret_cast<__nv_bfloat162*>(p + plane_stride + e)[0] = __halves2bfloat162(al, bl);
   }
+}
+
+// plane pl of the BF16 hi + lo split of x (0: hi = x rounded; 1: lo = x - hi rounded)
+__device__ __forceinline__ __nv_bfloat16 bf16_part(float x, int pl) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  return pl == 0 ? h : __float2bfloat16_rn(x - __bfloat162float(h));
+}
+// two BF16 values as one 32-bit word, lo first in memory
+__device__ __forceinline__ uint32_t bf16_pair(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 // store 16 consecutive values of a row (element e, a multiple of 16) in every plane
@@ -157,239 +152,9 @@ struct EpiSpread {
   const int* slot_site;
 };
 
-template <int MODE, int PREC>
-__global__ void __launch_bounds__(128, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-          int kblocks, const int* __restrict__ a_batch, const int* __restrict__ b_batch,
-          const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
-          EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
-  using P = Prec<PREC>;
-  using TL = Tile<PREC>;
-  constexpr int STAGES = stages_of<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ float red[BN / 2];
-  const int z = blockIdx.z;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int nv = n_valid[z];
-  if (n0 >= nv || (m_valid && m0 >= m_valid[z])) return;
-  const uint32_t raw = tc::smem_u32(smem_raw);
-  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * TL::STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(full + s, 1);
-      tc::mbar_init(empty + s, 1);
-    }
-    tc::mbar_init(done, 1);
-    tc::fence_barrier_init();
-    tc::tma_prefetch(&ta);
-    tc::tma_prefetch(&tb);
-  }
-  if (warp == 0) tc::tmem_alloc(tmem_holder, BN);
-  if (MODE == 1)
-    for (int i = threadIdx.x; i < BN / 2; i += blockDim.x) red[i] = 0.f;
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tmem_holder;
-  bool ok = true;
-
-  // stage layout: A plane 0 .. PL-1, then B plane 0 .. PL-1 (each 1024-byte aligned)
-  if (warp == 0 && lane == 0) {
-    const int ab = a_batch[z], bb = b_batch[z];
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES) ok &= tc::mbar_wait(empty + s, ((kb / STAGES) - 1) & 1);
-      uint8_t* st = sm + s * TL::STAGE_BYTES;
-      tc::mbar_arrive_expect_tx(full + s, TL::STAGE_BYTES);
-#pragma unroll
-      for (int pl = 0; pl < PL; ++pl) {
-        tc::tma_load_4d(st + pl * TL::A_BYTES, &ta, full + s, kb * BK, m0, pl, ab);
-        tc::tma_load_4d(st + PL * TL::A_BYTES + pl * TL::B_BYTES, &tb, full + s, kb * BK, n0, pl,
-                        bb);
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      ok &= tc::mbar_wait(full + s, (kb / STAGES) & 1);
-      tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(sm + s * TL::STAGE_BYTES);
-      const uint32_t sb = sa + PL * TL::A_BYTES;
-      // each MMA consumes 32 bytes of K: 8 TF32 or 16 BF16 elements
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
-        if constexpr (PREC == EELS_TC_TF32) {
-          tc::mma_tf32(tmem, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32), P::IDESC,
-                       acc);
-        } else {
-          const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
-          const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
-          tc::mma_f16(tmem, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
-          tc::mma_f16(tmem, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
-          tc::mma_f16(tmem, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
-        }
-      }
-      tc::mma_commit(empty + s);
-    }
-    tc::mma_commit(done);
-  }
-  __syncwarp();
-  ok &= tc::mbar_wait(done, 0);
-  tc::fence_after_sync();
-
-  const int row = m0 + warp * 32 + lane;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  if constexpr (MODE == 0) {
-    const int64_t rbase = (int64_t)z * es.z_stride + (int64_t)row * es.row_pitch;
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tc::tmem_ld16(trow + c, v);
-      const int col = n0 + c;
-      if (row < es.rows && col < es.cols) put16<PREC>(es.out, es.plane_stride, rbase + col, v);
-    }
-  } else if constexpr (MODE == 2) {
-    // Chunks of 32 columns (16 pixels): every thread forms its two output rows
-    // (H_t Y and -i H_t Y) for a group of channels in shared memory (the pipeline
-    // buffers, idle now), then the CTA writes whole 32-element row segments, so each
-    // warp store covers full 32-byte sectors instead of 32 scattered rows.
-    using T = typename P::T;
-    constexpr int CW = 32;                                   // columns per chunk
-    constexpr int RB = CW * (int)sizeof(T);                  // bytes of a row segment
-    constexpr int PITCH = RB + 16;                           // staging row pitch
-    constexpr int TILE = 2 * BM * PITCH;                     // one channel, one plane
-    constexpr int SEGS = RB / 16;                            // 16-byte parts of a segment
-    const int tg_max = (int)((size_t)STAGES * TL::STAGE_BYTES / ((size_t)PL * TILE));
-    const int site = ey.slot_site[z];
-    const int rows_out = 2 * ey.rows;                        // rows of BV per channel
-    uint8_t* stg = sm;
-    for (int c = 0; c < BN && n0 + c < es.cols; c += CW) {
-      for (int t0 = 0; t0 < ey.n_types; t0 += tg_max) {
-        const int tg = min(tg_max, ey.n_types - t0);
-        float v[CW];
-        tc::tmem_ld16(trow + c, v);
-        tc::tmem_ld16(trow + c + 16, v + 16);
-        for (int tt = 0; tt < tg; ++tt) {
-          const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0 + tt) * ey.P;
-          float hy[CW], mhy[CW];
-#pragma unroll
-          for (int q = 0; q < CW / 2; ++q) {
-            const int pp = (n0 + c) / 2 + q;
-            const float2 h = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
-            const float2 y = cmul(h, make_float2(v[2 * q], v[2 * q + 1]));
-            hy[2 * q] = y.x;
-            hy[2 * q + 1] = y.y;
-            mhy[2 * q] = y.y;
-            mhy[2 * q + 1] = -y.x;
-          }
-          const int rr = 2 * (warp * 32 + lane);
-          uint8_t* d0 = stg + (size_t)(tt * PL) * TILE + (size_t)rr * PITCH;
-          if constexpr (PREC == EELS_TC_TF32) {
-            float4* a = reinterpret_cast<float4*>(d0);
-            float4* b = reinterpret_cast<float4*>(d0 + PITCH);
-#pragma unroll
-            for (int q = 0; q < CW / 4; ++q) {
-              a[q] = make_float4(tc::to_tf32(hy[4 * q]), tc::to_tf32(hy[4 * q + 1]),
-                                 tc::to_tf32(hy[4 * q + 2]), tc::to_tf32(hy[4 * q + 3]));
-              b[q] = make_float4(tc::to_tf32(mhy[4 * q]), tc::to_tf32(mhy[4 * q + 1]),
-                                 tc::to_tf32(mhy[4 * q + 2]), tc::to_tf32(mhy[4 * q + 3]));
-            }
-          } else {
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              const float* src = half ? mhy : hy;
-              __align__(16) __nv_bfloat16 hi[CW], lo[CW];
-#pragma unroll
-              for (int q = 0; q < CW; ++q) {
-                hi[q] = __float2bfloat16_rn(src[q]);
-                lo[q] = __float2bfloat16_rn(src[q] - __bfloat162float(hi[q]));
-              }
-              uint4* dh = reinterpret_cast<uint4*>(d0 + half * PITCH);
-              uint4* dl = reinterpret_cast<uint4*>(d0 + TILE + half * PITCH);
-#pragma unroll
-              for (int q = 0; q < SEGS; ++q) {
-                dh[q] = reinterpret_cast<const uint4*>(hi)[q];
-                dl[q] = reinterpret_cast<const uint4*>(lo)[q];
-              }
-            }
-          }
-        }
-        __syncthreads();
-        // coalesced copy-out: item = (channel, plane, row, 16-byte part)
-        const int items = tg * PL * 2 * BM * SEGS;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-          const int part = it % SEGS;
-          const int rr = (it / SEGS) % (2 * BM);
-          const int tp = it / (SEGS * 2 * BM);               // tt * PL + pl
-          const int tt = tp / PL, pl = tp % PL;
-          const int orow = 2 * m0 + rr;
-          if (orow >= rows_out) continue;
-          const int64_t e = ((int64_t)z * ey.n_types + t0 + tt) * ey.z_stride +
-                            (int64_t)pl * ey.plane_stride + (int64_t)orow * ey.row_pitch + n0 + c;
-          const uint4 val = *reinterpret_cast<const uint4*>(stg + (size_t)tp * TILE +
-                                                            (size_t)rr * PITCH + part * 16);
-          reinterpret_cast<uint4*>(static_cast<T*>(ey.bv) + e)[part] = val;
-        }
-        __syncthreads();
-      }
-    }
-  } else {
-    const bool live = row < ea.rows;
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tc::tmem_ld16(trow + c, v);
-      float p[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        p[q] = live ? fmaf(v[2 * q], v[2 * q], v[2 * q + 1] * v[2 * q + 1]) : 0.f;
-      // reduce-scatter over the 32 rows of the warp: halve the value set at each of the
-      // lane bits 4, 3, 2, then sum over bits 1, 0.  Lane L ends with the warp total of
-      // value ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
-      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-      float r4[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float send = b4 ? p[q] : p[q + 4];
-        r4[q] = (b4 ? p[q + 4] : p[q]) + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-      float r2[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float send = b3 ? r4[q] : r4[q + 2];
-        r2[q] = (b3 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      float r1 = (b2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r2[0] : r2[1], 4);
-      r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
-      r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
-      if ((lane & 3) == 0) atomicAdd(&red[c / 2 + (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)], r1);
-    }
-    __syncthreads();
-    const int s = ea.z_site[z];
-    const int nx = ea.xcnt[s];
-    for (int i = threadIdx.x; i < BN / 2; i += blockDim.x) {
-      const int r = n0 / 2 + i;
-      if (2 * r < nv) {
-        const int ix = ea.xlist[ea.xoff[s] + r % nx];
-        const int iy = ea.ylist[ea.yoff[s] + r / nx];
-        const int64_t idx = ((int64_t)ea.z_type[z] * ea.n_sy + iy) * ea.n_sx + ix;
-        atomicAdd(ea.map + idx, (double)red[i]);
-      }
-    }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, BN);
-  if (!ok && status) atomicExch(status, 1);
-}
-
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised TF32 form of the same three GEMMs.  One CTA per SM walks
+// Persistent, warp-specialised kernel of the three GEMMs (both precisions).  Tile
+// BM x BN = 128 x 256, K blocks of 128 bytes per row.  One CTA per SM walks
 // the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 issues the TMA loads, warp 1
 // the MMAs, warps 2-9 run the epilogue (two per TMEM lane quarter, each pair splitting
 // the 256 columns).  The accumulator is double-buffered in TMEM (2 x 256 columns), so
@@ -405,18 +170,26 @@ constexpr int CW = 32;                          // GEMM-Y epilogue chunk (column
 constexpr int TILE = 2 * BM * CW * 4;           // one chunk of one channel: 256 rows x 128 B,
                                                 // 128-byte swizzled, stored by one TMA box
 constexpr int TG = 1;                           // channels staged at once per column half
+// BF16 GEMM-Y stages one plane of a 32-column chunk at a time: 256 rows x 64 bytes
+// (32 BF16 values), 64-byte swizzled, 16 KB per column half.
+constexpr int TILE_BF16 = 2 * BM * 32 * 2;
 // TF32 stages are 48 KB (4, or 3 beside the GEMM-Y staging); BF16 hi + lo stages are
-// 96 KB (2).  GEMM-Y runs here in TF32 only.
+// 96 KB (2, also beside the smaller BF16 GEMM-Y staging: 2 x 96 + 2 x 16 KB).
 template <int MODE, int PREC>
 __host__ __device__ constexpr int stages() {
   return PREC == EELS_TC_TF32 ? (MODE == 2 ? 3 : 4) : 2;
 }
-template <int MODE>
-__host__ __device__ constexpr size_t staging() { return MODE == 2 ? (size_t)2 * TG * TILE : 0; }
+template <int MODE, int PREC>
+__host__ __device__ constexpr size_t staging_half() {
+  return MODE != 2 ? 0 : PREC == EELS_TC_TF32 ? (size_t)TG * TILE : (size_t)TILE_BF16;
+}
 template <int MODE, int PREC>
 __host__ __device__ constexpr size_t smem() {
-  return (size_t)stages<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + staging<MODE>() + 1024 + 256;
+  return (size_t)stages<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + 2 * staging_half<MODE, PREC>() +
+         1024 + 256;
 }
+static_assert(smem<2, EELS_TC_BF16X3>() + (BN / 2) * 4 + 16 <= 232448,
+              "BF16 GEMM-Y stages and staging exceed the shared memory of a CTA");
 }  // namespace ws
 
 // named barrier of the four epilogue warps of one column half (ids 1 and 2)
@@ -431,7 +204,6 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
              const int* __restrict__ a_batch, const int* __restrict__ b_batch,
              const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
              EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
-  static_assert(MODE != 2 || PREC == EELS_TC_TF32, "GEMM-Y runs the persistent form in TF32");
   using P = Prec<PREC>;
   using TL = Tile<PREC>;
   constexpr int S = ws::stages<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
@@ -441,7 +213,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* stg = sm + S * TL::STAGE_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(stg + ws::staging<MODE>());
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + 2 * ws::staging_half<MODE, PREC>());
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;
   uint64_t* acc_empty = acc_full + 2;
@@ -568,7 +340,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
     const int half = (warp - 2) >> 2;         // column half of the tile
     const int te = threadIdx.x - 64 - 128 * half;   // 0 .. 127 within the half
     const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
-    uint8_t* stg_h = stg + (size_t)half * ws::TG * ws::TILE;
+    uint8_t* stg_h = stg + (size_t)half * ws::staging_half<MODE, PREC>();
     int i = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       int z, n0, m0;
@@ -591,6 +363,55 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           const int col = n0 + c;
           if (row < es.rows && col < es.cols)
             put16<PREC>(es.out, es.plane_stride, rbase + col, v);
+        }
+      } else if constexpr (MODE == 2 && PREC == EELS_TC_BF16X3) {
+        // chunks of 32 columns (16 pixels): each thread forms its two rows (H_t Y and
+        // -i H_t Y) and writes them, hi plane then lo plane, into the half's staging tile
+        // (64-byte rows, 64-byte swizzle); one thread of the half stores each plane with one
+        // TMA box, and the tile is rewritten only after that store has read it
+        const int site = ey.slot_site[z];
+        const int rr = 2 * (q4 * 32 + lane);
+        for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += 32) {
+          for (int t0 = 0; t0 < ey.n_types; ++t0) {
+            float v[32];
+            tc::tmem_ld16(trow + c, v);
+            tc::tmem_ld16(trow + c + 16, v + 16);
+            const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0) * ey.P;
+            float2 y[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int pp = (n0 + c) / 2 + k;
+              const float2 h = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
+              y[k] = cmul(h, make_float2(v[2 * k], v[2 * k + 1]));
+            }
+            for (int pl = 0; pl < 2; ++pl) {
+              if (te == 0) tc::bulk_wait_read();
+              epi_sync(half);
+              uint8_t* r0 = stg_h + (size_t)rr * 64;
+              uint8_t* r1 = r0 + 64;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {   // 16-byte chunk q: pixels 4q .. 4q + 3
+                uint32_t a[4], b[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float2 u = y[4 * q + e];
+                  a[e] = bf16_pair(bf16_part(u.x, pl), bf16_part(u.y, pl));
+                  b[e] = bf16_pair(bf16_part(u.y, pl), bf16_part(-u.x, pl));
+                }
+                // chunk q of 64-byte row r sits at chunk q ^ ((r >> 1) & 3) (64-byte swizzle)
+                *reinterpret_cast<uint4*>(r0 + ((q ^ ((rr >> 1) & 3)) << 4)) =
+                    make_uint4(a[0], a[1], a[2], a[3]);
+                *reinterpret_cast<uint4*>(r1 + ((q ^ (((rr + 1) >> 1) & 3)) << 4)) =
+                    make_uint4(b[0], b[1], b[2], b[3]);
+              }
+              tc::fence_async_shared();
+              epi_sync(half);
+              if (te == 0) {
+                tc::tma_store_4d(&tv, stg_h, n0 + c, 2 * m0, pl, z * ey.n_types + t0);
+                tc::bulk_commit();
+              }
+            }
+          }
         }
       } else if constexpr (MODE == 2) {
         // chunks of 32 columns: each thread forms its two rows (H_t Y and -i H_t Y) in the
@@ -945,7 +766,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 4D tensor map (k, rows, plane, batch) over a K-major buffer; box (BK, box_rows, 1, 1),
 // 128-byte swizzle; out-of-range rows read as zero.
 template <int PREC>
-cudaError_t make_map(CUtensorMap* map, void* base, int k, int rows, int batch, int box_rows) {
+cudaError_t make_map(CUtensorMap* map, void* base, int k, int rows, int batch, int box_rows,
+                     int box_k = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B) {
   using P = Prec<PREC>;
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
@@ -953,22 +775,11 @@ cudaError_t make_map(CUtensorMap* map, void* base, int k, int rows, int batch, i
   cuuint64_t dims[4] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)P::PLANES, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)k * es, (cuuint64_t)k * es * rows,
                            (cuuint64_t)k * es * rows * P::PLANES};
-  cuuint32_t box[4] = {(cuuint32_t)P::BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)(box_k > 0 ? box_k : P::BK), (cuuint32_t)box_rows, 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = fn(map, P::DT, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-template <int PREC>
-cudaError_t set_attrs() {
-  static std::atomic<uint64_t> d0{0}, d1{0}, d2{0};
-  cudaError_t e = smem_attr_once(k_tc_gemm<0, PREC>, smem_of<0, PREC>(), d0);
-  if (e != cudaSuccess) return e;
-  e = smem_attr_once(k_tc_gemm<1, PREC>, smem_of<1, PREC>(), d1);
-  if (e != cudaSuccess) return e;
-  return smem_attr_once(k_tc_gemm<2, PREC>, smem_of<2, PREC>(), d2);
 }
 
 template <int PREC>
@@ -1011,22 +822,15 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
                         const EpiAbs2& ea, const EpiSpread& ey, int* status, cudaStream_t st,
                         int valid_tiles) {
   if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
-  if constexpr (PREC == EELS_TC_TF32 || MODE != 2) {
-    static std::atomic<uint64_t> attr{0};
-    cudaError_t e = smem_attr_once(k_tc_gemm_ws<MODE, PREC>, ws::smem<MODE, PREC>(), attr);
-    if (e != cudaSuccess) return e;
-    const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
-    if (tiles <= 0) return cudaSuccess;
-    const int grid = std::min(tiles, sm_count());
-    k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
-        ta, tb, tv, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
-        status);
-  } else {
-    cudaError_t e = set_attrs<PREC>();
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<MODE, PREC><<<dim3(gx, gy, gz), 128, smem_of<MODE, PREC>(), st>>>(
-        ta, tb, kblocks, a_batch, b_batch, n_valid, m_valid, es, ea, ey, status);
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = smem_attr_once(k_tc_gemm_ws<MODE, PREC>, ws::smem<MODE, PREC>(), attr);
+  if (e != cudaSuccess) return e;
+  const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = std::min(tiles, sm_count());
+  k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
+      ta, tb, tv, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
+      status);
   return cudaGetLastError();
 }
 
@@ -1095,9 +899,11 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
                b.n_types, b.H, b.h_mul, b.slot_site};
   // store map of GEMM-Y's output: BV rows (2 per probe) in boxes of 32 columns x 256 rows
+  // of one plane (TF32: 128-byte rows, 128-byte swizzle; BF16: 64-byte rows and swizzle)
   CUtensorMap mBV;
-  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, 2 * BM)) !=
-      cudaSuccess)
+  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, 2 * BM, 32,
+                          PREC == EELS_TC_TF32 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                               : CU_TENSOR_MAP_SWIZZLE_64B)) != cudaSuccess)
     return e;
   return launch_gemm<2, PREC>(mAY, mBY, mBV, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
                               (b.nr_cap + BM - 1) / BM, b.n_sites, b.tiles_y, b.a_batch_y,
