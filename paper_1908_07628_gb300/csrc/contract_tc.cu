@@ -559,7 +559,7 @@ struct WindowWalk {
 // Beams of S_out per block of the S_out gather, and probe rows per block of the
 // probe-row gather: enough loads per thread to cover the memory latency.
 constexpr int kSoutBeams = 4;
-constexpr int kArowRows = 4;
+constexpr int kArowRows = 16;
 
 // A1[slot][plane][d][2p + c] = Sout[d][pixel p of the window of site slot_site[slot]];
 // a block takes kSoutBeams beams d of one site.
@@ -669,7 +669,8 @@ __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __r
 }
 
 // AY[slot][plane][r][2j + c] = a_r[j] (interleaved), a_r[j] = axT[ix(r)][j] ayT[iy(r)][j];
-// a block takes kArowRows rows r of one site.
+// a block takes kArowRows rows r of one site (their phase-table rows are looked up once,
+// by the first kArowRows threads) and writes them four at a time.
 template <int PREC>
 __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __restrict__ ayT,
                                int n_in, const int* __restrict__ slot_site,
@@ -678,34 +679,37 @@ __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __r
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
                                int nr_cap, void* __restrict__ AY, int k2p) {
   constexpr int PL = Prec<PREC>::PLANES;
+  __shared__ int s_ix[kArowRows], s_iy[kArowRows];
   const int rb = blockIdx.x * kArowRows, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
   const int r_end = min((nr + BM - 1) / BM * BM, nr_cap);   // rows of M tiles GEMM-Y reads
-  if (rb >= r_end) return;
-  const int64_t pstride = (int64_t)nr_cap * k2p;
-  const float2* axr[kArowRows];
-  const float2* ayr[kArowRows];
-  bool live[kArowRows];
-#pragma unroll
-  for (int i = 0; i < kArowRows; ++i) {
-    const int r = rb + i;
-    live[i] = r < nr;
-    const int ix = live[i] ? xlist[xoff[s] + r % nx] : 0;
-    const int iy = live[i] ? ylist[yoff[s] + r / nx] : 0;
-    axr[i] = axT + (int64_t)ix * n_in;
-    ayr[i] = ayT + (int64_t)iy * n_in;
+  if (rb >= r_end) return;                                   // the same for the whole block
+  if (threadIdx.x < kArowRows) {
+    const int r = rb + threadIdx.x;
+    s_ix[threadIdx.x] = r < nr ? xlist[xoff[s] + r % nx] : -1;   // -1: a zero row
+    s_iy[threadIdx.x] = r < nr ? ylist[yoff[s] + r / nx] : -1;
   }
-  for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
-    float2 a[kArowRows];
+  __syncthreads();
+  const int rows = min(kArowRows, r_end - rb);
+  const int64_t pstride = (int64_t)nr_cap * k2p;
+  const int64_t base = (int64_t)slot * PL * pstride + (int64_t)rb * k2p;
+  for (int i0 = 0; i0 < rows; i0 += 4) {
+    for (int j = threadIdx.x; j < k2p / 2; j += blockDim.x) {
+      float2 a[4];
 #pragma unroll
-    for (int i = 0; i < kArowRows; ++i)
-      a[i] = (live[i] && j < n_in) ? cmul(axr[i][j], ayr[i][j]) : make_float2(0.f, 0.f);
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        const int ix = i < rows ? s_ix[i] : -1, iy = i < rows ? s_iy[i] : -1;
+        a[u] = (ix >= 0 && j < n_in)
+                   ? cmul(axT[(int64_t)ix * n_in + j], ayT[(int64_t)iy * n_in + j])
+                   : make_float2(0.f, 0.f);
+      }
 #pragma unroll
-    for (int i = 0; i < kArowRows; ++i)
-      if (rb + i < r_end)
-        put2<PREC>(AY, pstride, (int64_t)slot * PL * pstride + (int64_t)(rb + i) * k2p + 2 * j,
-                   a[i].x, a[i].y);
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < rows)
+          put2<PREC>(AY, pstride, base + (int64_t)(i0 + u) * k2p + 2 * j, a[u].x, a[u].y);
+    }
   }
 }
 
