@@ -25,7 +25,7 @@ namespace eels {
 
 namespace {
 
-constexpr int kRowWarps = 8;   // rows per CTA in the row pass
+constexpr int kRowWarps = 4;   // warps per CTA in the row pass (ROWS rows each)
 constexpr int kColCB = 8;      // columns per CTA in the column pass (one warp each)
 
 template <int N>
@@ -123,11 +123,11 @@ k_row_pass(const float2* __restrict__ W, float2* __restrict__ Phi,
   row_pass_body<N>(W, Phi, t_slice, conj_t, store_mode, S, s_waves, s_stride, fft_out, tw);
 }
 
-// The 768 plan (radix 24 then 32) would take 132 registers and so one CTA per SM; this
-// form caps it at 128 (two CTAs) without spills.
+// The 768 plan (radix 24 then 32) would take 132 registers, leaving an SM fewer than 16
+// warps; this form caps it at 128 registers (16 warps per SM) without spills.
 template <int N>
-__global__ void __launch_bounds__(kRowWarps * 32, 2)
-k_row_pass_2cta(const float2* __restrict__ W, float2* __restrict__ Phi,
+__global__ void __launch_bounds__(kRowWarps * 32, 16 / kRowWarps)
+k_row_pass_capped(const float2* __restrict__ W, float2* __restrict__ Phi,
                 const float2* __restrict__ t_slice, int conj_t, int store_mode,
                 float2* __restrict__ S, int s_waves, int64_t s_stride, int fft_out,
                 const float2* __restrict__ tw) {
@@ -430,7 +430,7 @@ cudaError_t row_pass_n(int n_waves, const float2* W, float2* Phi, const float2* 
   constexpr int ROWS = RegFFT<N>::ROWS;
   const size_t smem = (size_t)kRowWarps * ROWS * spad_len(N) * sizeof(float2);
   auto kern = [] {
-    if constexpr (N == 768) return k_row_pass_2cta<N>;
+    if constexpr (N == 768) return k_row_pass_capped<N>;
     else return k_row_pass<N>;
   }();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
