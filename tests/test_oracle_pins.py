@@ -197,6 +197,56 @@ def test_thin_single_atom_limit_is_fourier_transform_of_H_times_probe():
                 assert abs(f * f * tot - I[m, iy, ix]) < 1e-12 * I[m].max()
 
 
+@pytest.mark.parametrize("f", [2, 3])
+def test_thin_single_atom_limit_with_prism_windows(f):
+    """f > 1, n_z = 1, v = 0 (Sec. III, Sec. IV C): probe R sees the site only when the
+    minimum-image displacement r_s - R lies in [-L/2f, L/2f) on both axes; there I(R) is
+    f^2 sum_d of the direct-sum Fourier transform of H times the f-lattice probe, elsewhere
+    zero.  The window test and the sums are written out here, apart from the oracle."""
+    n, L = 32, 6.0
+    wl = _tiny(n=n, f=f, n_z=1, n_sites=1, w=10, alpha=0.02, beta=0.03, cell=L, scan_n=16,
+               seed=1)
+    wl.vproj[:] = 0.0
+    wl.site_slice[:] = 0
+    I = ms.quadratic_map(wl)
+    nh = n // 2
+    bp, bq = ms.lattice_beams(n, L, wl.lam, f, wl.alpha)
+    dp, dq = ms.lattice_beams(n, L, wl.lam, f, wl.beta)
+    c = f / math.sqrt(bp.size)
+    rx, ry = wl.scan_positions()
+    half = L / (2 * f)
+
+    def inside(s, r):
+        d = s - r
+        d -= L * math.floor(d / L + 0.5)
+        return -half <= d < half
+
+    my, mx = np.meshgrid(np.arange(nh), np.arange(nh), indexing="ij")
+    X, Y = 2 * mx * L / n, 2 * my * L / n
+    rows = (wl.win_y0[0] + np.arange(wl.w)) % nh
+    cols = (wl.win_x0[0] + np.arange(wl.w)) % nh
+    seen = set()
+    for m in range(wl.n_types):
+        win = np.zeros((nh, nh), dtype=complex)
+        win[np.ix_(rows, cols)] = wl.H[0, m]
+        for iy in range(rx.size):
+            for ix in range(rx.size):
+                hit = inside(wl.site_x[0], rx[ix]) and inside(wl.site_y[0], ry[iy])
+                seen.add(hit)
+                if not hit:
+                    assert I[m, iy, ix] == 0.0
+                    continue
+                psi = np.zeros((nh, nh), dtype=complex)
+                for p, q in zip(bp, bq):
+                    psi += c * np.exp(2j * math.pi * f * (p * (X - rx[ix]) + q * (Y - ry[iy])) / L) / n
+                tot = 0.0
+                for p, q in zip(dp, dq):
+                    amp = (4.0 / n) * np.sum(win * psi * np.exp(-2j * math.pi * f * (p * mx + q * my) / nh))
+                    tot += abs(amp) ** 2
+                assert abs(f * f * tot - I[m, iy, ix]) < 1e-12 * I[m].max()
+    assert seen == {True, False}   # the scan reaches both sides of the window edge
+
+
 @pytest.mark.parametrize("n,f,cell,alpha,beta", [(16, 1, 4.0, 0.0138, 0.018),
                                                  (32, 2, 8.0, 0.0138, 0.018),
                                                  (32, 1, 6.0, 0.02, 0.03)])
