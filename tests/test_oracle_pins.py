@@ -128,6 +128,30 @@ def test_paraxial_gaussian_beam_matches_fresnel_solution():
     assert np.abs(y - ref).max() < 1e-10
 
 
+def test_transmission_phase_focuses_like_a_converging_lens():
+    """Eq. 3 with the propagator: a slice whose projected potential falls off as -kappa r^2
+    is a thin converging lens of focal length pi / (lambda sigma kappa).  A Gaussian beam
+    through it and 50 A of free space follows the complex-width solution, brightening on
+    axis towards the focus (with the phase sign reversed it would spread instead)."""
+    n, L, lam, dz, nz, w0 = 256, 16.0, 0.02508, 2.5, 20, 0.5
+    sigma = 7.2886e-4
+    kappa = math.pi / (lam * sigma * 50.0)          # focal length 50 A
+    x = np.arange(n) * L / n
+    d = x - L / 2
+    X, Y = np.meshgrid(d, d)
+    r2 = X ** 2 + Y ** 2
+    psi = np.exp(-r2 / (2 * w0 ** 2)).astype(np.complex128)
+    P = ms.propagator(n, L, lam, dz)
+    y = ms.slice_step(psi, ms.transmission(-kappa * r2, sigma), P)
+    for _ in range(nz - 1):
+        y = ms.slice_step(y, np.ones((n, n)), P)
+    a = 1 / (2 * w0 ** 2) + 1j * sigma * kappa        # exp(-a r^2) after the lens
+    w2 = 1 / (2 * a) + 1j * lam * nz * dz / (2 * math.pi)
+    ref = (1 / (2 * a * w2)) * np.exp(-r2 / (2 * w2))
+    assert np.abs(y - ref).max() < 1e-10
+    assert abs(y[n // 2, n // 2]) ** 2 > 1.5
+
+
 def test_adjoint_of_slice_step():
     rng = np.random.default_rng(4)
     n = 48
