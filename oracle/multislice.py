@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring): nothing in the CUDA
 library imports or calls this module.
 
-Conventions (the paper fixes the physics; where it is silent the reading is
-stated here and in the design notes):
+Conventions (the paper fixes the physics; where it is silent the reading taken
+is stated here):
 
 * Grid: N x N pixels over an L x L cell; arrays are [y][x].  Signed frequency
   indices p, q in FFT order; k = (p/L, q/L).  Forward transform uses
