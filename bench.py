@@ -12,6 +12,7 @@ Under torchrun (N > 1) every rank runs an independent replica of the workload
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import multiprocessing as mp
@@ -31,11 +32,8 @@ import specimen as sp  # noqa: E402
 
 METRIC = "EELS map pixel-slices/s"
 UNIT = "pixel-slices/s"
-DEFAULT_WORKLOAD = "rocksalt_fp32"
+DEFAULT_WORKLOAD = "nanoparticle"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
-SMS, FP32_LANES = 152, 128
-TF32_PER_BF16 = 1.1 / 2.25
 
 
 def _peaks():
@@ -102,20 +100,34 @@ class ClockSampler:
 # CPU oracle sample (the conventional algorithm, FP64, as it stands)
 # ---------------------------------------------------------------------------
 
-def _oracle_probe_sample(args):
-    """One probe of the conventional oracle with the sites of the deepest slice that
-    holds any site in the probe's window (a few hundred multislice operations)."""
-    name, iy, ix = args
+_POOL_WL = None
+
+
+def _pool_init(name):
+    """Worker initialiser: build the workload once per process."""
+    global _POOL_WL
     import specimen as sp_
+    os.environ["OMP_NUM_THREADS"] = "1"
+    _POOL_WL = sp_.WORKLOADS[name]()
+
+
+def _oracle_probe_sample(args):
+    """One probe of the conventional oracle over the last `tail` slices of the specimen with
+    the deepest `max_sites` sites of its window there: a few tens of multislice operations,
+    each the same transmit-FFT-propagate-IFFT step the full run repeats."""
+    iy, ix, tail, max_sites = args
     from oracle import multislice as ms
-    wl = sp_.WORKLOADS[name]()
+    wl = _POOL_WL
+    first = max(0, wl.n_z - tail)
     rx, ry = wl.scan_positions()
     seen = [s for s in range(wl.n_sites)
-            if ms.axis_in_window(wl.site_x[s], rx[ix], wl.cell, wl.f)
+            if wl.site_slice[s] >= first
+            and ms.axis_in_window(wl.site_x[s], rx[ix], wl.cell, wl.f)
             and ms.axis_in_window(wl.site_y[s], ry[iy], wl.cell, wl.f)]
-    deepest = max((int(wl.site_slice[s]) for s in seen), default=0)
-    keep = [s for s in seen if wl.site_slice[s] == deepest]
-    sub = wl.with_sites(keep)
+    seen.sort(key=lambda s: -int(wl.site_slice[s]))
+    sub = wl.with_sites(seen[:max_sites])
+    sub = dataclasses.replace(sub, vproj=wl.vproj[first:], n_z=wl.n_z - first,
+                              site_slice=(sub.site_slice - first).astype(np.int32))
     c = {}
     t0 = time.perf_counter()
     ms.quadratic_map(sub, positions=[(iy, ix)], counter=c)
@@ -134,37 +146,82 @@ def _full_probe_steps(wl, iy, ix):
     return steps
 
 
-def cpu_oracle_rate(wl_name, budget_procs=None):
-    """Pixel-slices/s of the FP64 conventional oracle on this host's cores.
+class OracleSampler:
+    """The FP64 conventional oracle on this host's cores, one worker process per core,
+    each holding the workload.  sample() runs one probe per worker (spread over the
+    scan) with the deepest sites of its window; the cost of the conventional algorithm
+    is exactly linear in its multislice count, so the full-workload rate is the sampled
+    time per operation times the full per-probe count."""
 
-    Sample: one probe per worker process (spread over the scan), each running the
-    conventional algorithm with only the sites of one deep slice of its window,
-    so every worker does a few hundred multislice operations.  The cost of the
-    conventional algorithm is exactly linear in its multislice count, so the
-    full-workload rate is the sampled time per operation times the full count.
-    """
+    def __init__(self, wl_name, procs=None, tail=8, max_sites=1):
+        self.name = wl_name
+        self.wl = sp.WORKLOADS[wl_name]()
+        self.procs = procs or os.cpu_count() or 1
+        self.tail = tail
+        self.max_sites = max_sites
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_pool_init,
+                                                 initargs=(wl_name,))
+        self.k = 0
+
+    def sample(self):
+        wl = self.wl
+        n_sx, n_sy = wl.scan[0], wl.scan[1]
+        jobs = []
+        for q in range(self.procs):
+            k = self.k * self.procs + q
+            jobs.append(((k * 7 + 3) % n_sy, (k * 13 + 5) % n_sx, self.tail, self.max_sites))
+        self.k += 1
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_probe_sample, jobs)
+        wall = time.perf_counter() - t0
+        ops = sum(s for _, s in res)
+        per_op = sum(t for t, _ in res) / ops            # seconds per op per core
+        full = float(np.mean([_full_probe_steps(wl, j[0], j[1]) for j in jobs]))
+        rate = self.procs * wl.n_z / (full * per_op)     # a core does n_z pixel-slices per probe
+        sample = (f"{self.procs} processes x 1 probe of {wl.name}: the conventional algorithm over "
+                  f"the last {self.tail} slices with the {self.max_sites} deepest sites of the "
+                  f"probe's window there ({ops} multislice ops, {wall:.1f} s wall); rate scaled "
+                  f"by the full per-probe count {full:.0f} ops")
+        return rate, sample, {"wall_s": wall, "ops": int(ops), "full_ops_per_probe": full}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_rate(wl_name, budget_procs=None):
+    """Pixel-slices/s of the FP64 conventional oracle on this host's cores (one sample)."""
+    smp = OracleSampler(wl_name, budget_procs)
+    try:
+        rate, sample, rec = smp.sample()
+    finally:
+        smp.close()
+    return rate, smp.procs, sample, rec
+
+
+def _oracle_full_probe(args):
+    name, iy, ix = args
+    import specimen as sp_
+    from oracle import multislice as ms
+    wl = sp_.WORKLOADS[name]()
+    return ms.quadratic_map(wl, positions=[(iy, ix)])[:, iy, ix]
+
+
+def cpu_oracle_full(wl_name):
+    """The whole map of a small workload with the FP64 conventional oracle, probes spread
+    over this host's cores: pixel-slices/s of a complete run, no extrapolation."""
     wl = sp.WORKLOADS[wl_name]()
-    cores = budget_procs or os.cpu_count() or 1
-    n_sx, n_sy = wl.scan[0], wl.scan[1]
-    jobs = []
-    for k in range(cores):
-        iy = (k * 7 + 3) % n_sy
-        ix = (k * 13 + 5) % n_sx
-        jobs.append((wl_name, iy, ix))
+    jobs = [(wl_name, iy, ix) for iy in range(wl.scan[1]) for ix in range(wl.scan[0])]
+    cores = min(os.cpu_count() or 1, len(jobs))
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_probe_sample, jobs)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_full_probe, jobs)
     wall = time.perf_counter() - t0
-    per_step = sum(t for t, _ in res) / sum(s for _, s in res)   # seconds per op per core
-    full = np.mean([_full_probe_steps(wl, j[1], j[2]) for j in jobs])
-    # one core finishes a probe (n_z pixel-slices) in full * per_step seconds
-    rate = cores * wl.n_z / (full * per_step)
-    sample = (f"{cores} processes x 1 probe of {wl.name}, sites of the deepest occupied slice only "
-              f"({sum(s for _, s in res)} multislice ops, {wall:.1f} s wall); rate scaled by "
-              f"the full per-probe count {full:.0f} ops")
-    return rate, cores, sample
+    return {"workload": wl.name, "value": wl.n_scan * wl.n_z / wall, "unit": UNIT,
+            "wall_s": wall, "cores": cores, "probes": len(jobs),
+            "sample": "complete map (every probe, every site), conventional FP64 algorithm"}
 
 
 # ---------------------------------------------------------------------------
@@ -341,7 +398,286 @@ def measured_traffic(kernel, n, waves):
     return None
 
 
-def gpu_arm(args, rank, world):
+# precision each workload's configuration names: the 1024^2 sphere and the 768^2 vacancy
+# crystal the BF16 hi + lo split, the 512^2 crystal ("FP32 on device") the TF32 tensor
+# cores with the hi + lo split (FP32-class), the small parity case the CUDA-core FP32 path
+CONFIG_PRECISION = {"rocksalt_small": "fp32", "rocksalt_fp32": "tf32", "rocksalt_vacancy": "bf16x3",
+                    "nanoparticle": "bf16x3", "nanoparticle_small": "bf16x3"}
+# extra workloads timed in the same run (same clocks record), each in its own precision
+EXTRA_CONFIGS = (("rocksalt_fp32", "tf32"), ("rocksalt_vacancy", "bf16x3"))
+# sampled-output accuracy against the FP64 oracle: three sites at three depths near the
+# first probe, the m = 0 channel, the conventional algorithm at two probes
+ORACLE_SAMPLES = {
+    "rocksalt_fp32": ((0, 21, 39), ((16, 16), (3, 29))),
+    "rocksalt_vacancy": ((0, 40, 79), ((16, 16), (2, 29))),
+    "nanoparticle": ((12, 25, 44), ((64, 64), (60, 70))),
+    "nanoparticle_small": ((4, 10, 17), ((24, 24), (20, 28))),
+    "rocksalt_small": ((0, 2, 5), ((3, 3), (5, 2))),
+}
+
+
+def workload_config(wl, n_in, n_out, precision, association, world):
+    """The configuration dict both arms report for a workload."""
+    return {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "cell_A": wl.cell,
+            "n_in": int(n_in), "n_out": int(n_out), "w": wl.w, "n_sites": int(wl.n_sites),
+            "scan": [int(wl.scan[0]), int(wl.scan[1])], "n_types": int(wl.n_types),
+            "precision": precision, "association": association,
+            "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (S_in alone is "
+                  f"{wl.n_z * n_in * (wl.n // 2) ** 2 * 8 / 1e9:.1f} GB)"}
+
+
+def oracle_sample_sub(wl, name):
+    """The sampled sub-workload (sites and m = 0 channel) and its probes."""
+    targets, probes = ORACLE_SAMPLES[name]
+    rx, ry = wl.scan_positions()
+    cx, cy = rx[probes[0][1]], ry[probes[0][0]]
+    chosen = []
+    for t in targets:
+        idx = np.nonzero(wl.site_slice == t)[0]
+        d2 = (wl.site_x[idx] - cx) ** 2 + (wl.site_y[idx] - cy) ** 2
+        chosen.append(int(idx[np.argmin(d2)]))
+    sub = wl.with_sites(chosen)
+    sub.H = np.ascontiguousarray(sub.H[:, min(1, sub.H.shape[1] - 1):][:, :1])
+    return sub, list(probes)
+
+
+def _oracle_probe(args):
+    """FP64 conventional oracle at one probe of a sampled sub-workload (a spawn worker)."""
+    name, k = args
+    import specimen as sp_
+    from oracle import multislice as ms
+    wl = sp_.WORKLOADS[name]()
+    sub, probes = oracle_sample_sub(wl, name)
+    iy, ix = probes[k]
+    t0 = time.perf_counter()
+    ref = ms.quadratic_map(sub, positions=[(iy, ix)])
+    return name, k, ref[:, iy, ix].tolist(), time.perf_counter() - t0
+
+
+def oracle_samples(names):
+    """Reference values of every sampled probe, computed on the host before CUDA starts."""
+    jobs = [(nm, k) for nm in names for k in range(len(ORACLE_SAMPLES[nm][1]))]
+    if not jobs:
+        return {}
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        res = pool.map(_oracle_probe, jobs)
+    out = {}
+    for nm, k, vals, sec in res:
+        out.setdefault(nm, {})[k] = (vals, sec)
+    return out
+
+
+def sampled_eps(g, ctx, wl, name, precision, ref, stream):
+    """eps of the GPU map against the FP64 oracle at the sampled probes (same sub-workload)."""
+    from oracle import multislice as ms
+    sub, probes = oracle_sample_sub(wl, name)
+    sm = g.build_smatrix_for(ctx, sub, stream=stream)
+    got = g.inelastic_map_for(ctx, sm, sub, precision=precision, stream=stream)
+    sm.free()
+    r = np.array([ref[k][0] for k in range(len(probes))])
+    t = np.array([got[:, iy, ix] for iy, ix in probes])
+    return {"eps_vs_fp64_oracle": float(ms.relative_error(r, t)),
+            "sample": f"{len(probes)} probes x 3 sites at depths {ORACLE_SAMPLES[name][0]}, "
+                      "m = 0 channel, full S-matrix; oracle: conventional FP64 algorithm",
+            "oracle_s": float(sum(ref[k][1] for k in range(len(probes))))}
+
+
+def measure_peaks(g, dev, seconds=3.0):
+    """TF32 (cuBLAS, torch fp32 matmul with TF32 allowed) burst and sustained, and the
+    FP32 FMA rate of the CUDA cores (eels_fp32_fma_rate), each with its SM clock."""
+    import torch
+    out = {}
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    prev = torch.get_float32_matmul_precision()
+    torch.set_float32_matmul_precision("high")        # TF32 tensor cores
+    try:
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out["tf32_tflops"] = 2.0 * n ** 3 / best / 1e12
+        clk = ClockSampler(dev)
+        clk.start()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 0
+        e0.record()
+        while time.perf_counter() - t0 < seconds:
+            for _ in range(8):
+                torch.matmul(a, b)
+            reps += 8
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        out["tf32_tflops_sustained"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        out["tf32_clocks"] = clk.stop()
+    finally:
+        torch.set_float32_matmul_precision(prev)
+    del a, b
+    torch.cuda.empty_cache()
+    clk = ClockSampler(dev)
+    clk.start()
+    rate = max(g.fp32_fma_rate(dev, 1 << 21) for _ in range(3))
+    out["fp32_fma_tflops"] = rate / 1e12
+    out["fp32_clocks"] = clk.stop()
+    out["how"] = ("tf32: torch.matmul fp32 8192^3 with TF32 allowed (cuBLAS), best of 10 (burst) "
+                  f"and back to back for {seconds:.0f} s (sustained); fp32: eels_fp32_fma_rate, "
+                  "independent FMA chains on every SM, best of 3")
+    return out
+
+
+def _timed_steps(step, k, stream, world, dev):
+    """k steps between CUDA events on the launch stream, barrier + synchronize on both
+    sides, SM clocks sampled meanwhile.  Returns (ms total, clocks)."""
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, clk
+
+
+def _profiled(ctx, step, k):
+    """Per-kernel CUDA-event times of k steps run apart from the timed region."""
+    import torch
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    ctx.profile_enable(True)
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_enable(False)
+    return ctx.profile_read()
+
+
+def _tensor_roof(kernel, wl, n_in, n_out, prof, steps, peak, peak_src):
+    """Roofline of a tensor-core kernel: three real products per useful product (hi + lo)."""
+    useful = contraction_flops(wl, n_in, n_out, kernel)
+    launches = prof[kernel]["launches"]
+    avg_s = prof[kernel]["ms"] / launches / 1e3
+    per_step = launches / steps
+    achieved = 3 * useful / per_step / avg_s / 1e12
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "useful_tflops": useful / per_step / avg_s / 1e12,
+            "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step,
+            "peak_source": peak_src}
+
+
+def _roofline(dom, wl, n_in, n_out, prof, steps, peaks, tpk, clk):
+    """Roofline entry of kernel `dom` from the profiled steps."""
+    if dom is None:
+        return None
+    alg = _algorithmic(wl, n_in, n_out, prof, steps)
+    launches = prof[dom]["launches"]
+    avg_s = prof[dom]["ms"] / launches / 1e3
+    per_step = launches / steps
+    if dom in alg:
+        bytes_launch = alg[dom][1] / per_step
+        achieved = bytes_launch / avg_s / 1e9
+        waves = n_out if "adjoint" in dom else n_in
+        return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": measured_traffic(dom, wl.n, waves), "algorithmic_bytes": bytes_launch,
+                "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+    if "bf16x3" in dom:
+        # the step runs for seconds: the sustained figure (measured under the power cap)
+        return _tensor_roof(dom, wl, n_in, n_out, prof, steps, peaks["bf16_tflops_sustained"],
+                            "measured bf16 sustained (MEASURED_PEAKS.json)")
+    if "tf32" in dom:
+        return _tensor_roof(dom, wl, n_in, n_out, prof, steps, tpk["tf32_tflops_sustained"],
+                            "measured tf32 sustained (cuBLAS, this run)")
+    flops = contraction_flops(wl, n_in, n_out, dom)
+    peak = tpk["fp32_fma_tflops"]
+    achieved = flops / per_step / avg_s / 1e12
+    return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3,
+            "peak_source": "measured fp32 FMA rate (eels_fp32_fma_rate, this run)"}
+
+
+def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
+    """Every multislice kernel against the HBM bound and the measured FP32 rate: per wave
+    and slice the row pass runs two N-point FFTs on N rows and one complex multiply per
+    pixel (10 N^2 log2 N + 6 N^2 flop), the column pass two FFTs on the N/2 band columns
+    and the propagator multiply (5 N^2 log2 N + 3 N^2 flop)."""
+    alg = _algorithmic(wl, n_in, n_out, prof, steps)
+    lg = math.log2(wl.n)
+    nn = float(wl.n) ** 2
+    row_full, row_last = 10 * nn * lg + 6 * nn, 5 * nn * lg + 6 * nn
+    col = 5 * nn * lg + 3 * nn
+    fft = {"row_pass": n_in * ((wl.n_z - 1) * row_full + row_last),
+           "row_pass_adjoint": n_out * ((wl.n_z - 1) * row_full + row_last),
+           "col_pass": n_in * (wl.n_z - 1) * col,
+           "col_pass_adjoint": n_out * (wl.n_z - 1) * col}
+    out = {}
+    for k in alg:
+        if k not in prof or prof[k]["ms"] <= 0:
+            continue
+        sec = prof[k]["ms"] / steps / 1e3
+        out[k] = {"achieved_gbs": alg[k][1] / sec / 1e9,
+                  "frac": alg[k][1] / sec / 1e9 / peaks["hbm_gbs"],
+                  "fft_tflops": fft[k] / sec / 1e12,
+                  "fp32_frac": fft[k] / sec / 1e12 / tpk["fp32_fma_tflops"]}
+    return out
+
+
+def _shares(prof, steps):
+    tot = sum(v["ms"] for v in prof.values())
+    return {k: {"launches_per_step": prof[k]["launches"] / steps,
+                "ms_per_step": prof[k]["ms"] / steps,
+                "share": prof[k]["ms"] / max(tot, 1e-9)} for k in sorted(prof)}
+
+
+def time_workload(g, ctx, wl, precision, steps, warmup, stream, world, dev):
+    """Warm-up, un-instrumented timed steps, then one profiled step.  Returns the figures."""
+    import torch
+    vdev = torch.from_numpy(wl.vproj).cuda()
+    Hdev = torch.from_numpy(wl.H).cuda()
+    mdev = torch.zeros((wl.n_types, wl.scan[1], wl.scan[0]), dtype=torch.float64, device="cuda")
+
+    def step():
+        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
+        g.inelastic_map_for(ctx, sm, wl, precision=precision, H=Hdev, out=mdev, stream=stream)
+        sm.free()
+
+    for _ in range(warmup):
+        step()
+    ms_total, clk = _timed_steps(step, steps, stream, world, dev)
+    prof = _profiled(ctx, step, 1)
+    del vdev, Hdev
+    return {"ms_total": ms_total, "clocks": clk, "prof": prof, "map": mdev}
+
+
+def gpu_arm(args, rank, world, ref_samples):
     import torch
     from paper_1908_07628_gb300 import build
     build.build()
@@ -350,49 +686,21 @@ def gpu_arm(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     wl = load_workload(args)
+    precision = args.precision or CONFIG_PRECISION.get(args.workload, "bf16x3")
     ctx = g.Context(dev)
     ctx.set_association(args.association)
     ctx.set_sout_scheme(args.sout_scheme)
     stream = torch.cuda.current_stream()
-    vdev = torch.from_numpy(wl.vproj).cuda()
-    Hdev = torch.from_numpy(wl.H).cuda()
-    mdev = torch.zeros((wl.n_types, wl.scan[1], wl.scan[0]), dtype=torch.float64, device="cuda")
-
-    def step():
-        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
-        g.inelastic_map_for(ctx, sm, wl, precision=args.precision, H=Hdev, out=mdev, stream=stream)
-        sm.free()
-
     n_in = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)
     n_out = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(dev)
-    clocks.start()
-    ctx.profile_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_total = e0.elapsed_time(e1)
-    ctx.profile_enable(False)
-    prof = ctx.profile_read()
-    clk = clocks.stop()
-    if world > 1:
-        torch.distributed.barrier()
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
+
+    # headline: un-instrumented timed steps; kernel shares from one profiled step after
+    res = time_workload(g, ctx, wl, precision, args.steps, args.warmup, stream, world, dev)
+    ms_step = res["ms_total"] / args.steps
     units = wl.n_scan * wl.n_z
     value = world * units / (ms_step / 1e3)
+    prof, clk = res["prof"], res["clocks"]
+    launches_per_step = sum(v["launches"] for v in prof.values())
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     vh = torch.from_numpy(wl.vproj).pin_memory().numpy()
@@ -401,7 +709,7 @@ def gpu_arm(args, rank, world):
 
     def e2e_step():
         sm = g.build_smatrix_for(ctx, wl, vproj=vh, stream=stream)
-        g.inelastic_map_for(ctx, sm, wl, precision=args.precision, H=Hh, out=mh, stream=stream)
+        g.inelastic_map_for(ctx, sm, wl, precision=precision, H=Hh, out=mh, stream=stream)
         sm.free()
 
     e2e_step()
@@ -414,146 +722,88 @@ def gpu_arm(args, rank, world):
     e2e_s = (time.perf_counter() - t0) / k_e2e
     h2d = wl.vproj.nbytes + wl.H.nbytes + wl.n_sites * (3 * 4 + 2 * 8)
     d2h = wl.n_types * wl.n_scan * 8
+    del vh, Hh
 
-    # accuracy of the timed precision against the FP32 CUDA-core path on the same
-    # workload (the FP32 path is pinned to the FP64 oracle by the parity tests)
-    acc = None
-    if rank == 0 and args.precision != "fp32" and not args.no_eps:
-        sm = g.build_smatrix_for(ctx, wl, vproj=vdev, stream=stream)
-        ref = g.inelastic_map_for(ctx, sm, wl, precision="fp32", H=Hdev, stream=stream)
-        sm.free()
-        got = mdev.cpu().numpy()
-        acc = {"eps_vs_fp32_path": float(np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2))),
-               "max_abs_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    out = {}
+    if rank == 0:
+        # measured denominators: TF32 tensor (cuBLAS) and the FP32 FMA rate, this run
+        tpk = measure_peaks(g, dev)
+        peaks = _peaks()
+        tot = {k: v["ms"] for k, v in prof.items()}
+        dom = max(tot, key=tot.get) if tot else None
+        out["roofline"] = _roofline(dom, wl, n_in, n_out, prof, 1, peaks, tpk, clk)
+        out["multislice_bounds"] = _multislice_bounds(wl, n_in, n_out, prof, 1, peaks, tpk)
+        out["kernels"] = _shares(prof, 1)
+        out["peaks_measured"] = tpk
+        acc = {}
+        if args.workload in ref_samples:
+            acc = sampled_eps(g, ctx, wl, args.workload, precision, ref_samples[args.workload],
+                              stream)
+        out["accuracy"] = acc
 
-    # quadratic algorithm on the same GPU, seeded probe sample, scaled per pixel-slice
-    quad = None
-    if rank == 0 and not args.no_quadratic:
-        rng = np.random.default_rng(16)
-        npos = min(args.quad_probes, wl.n_scan)
-        flat = rng.choice(wl.n_scan, size=npos, replace=False)
-        pos = [(int(i // wl.scan[0]), int(i % wl.scan[0])) for i in flat]
-        g.quadratic_reference_map_for(ctx, wl, positions=pos[:1], stream=stream)
-        torch.cuda.synchronize()
-        q0 = torch.cuda.Event(enable_timing=True)
-        q1 = torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        _, qsteps = g.quadratic_reference_map_for(ctx, wl, positions=pos, stream=stream)
-        q1.record(stream)
-        torch.cuda.synchronize()
-        qs = q0.elapsed_time(q1) / 1e3
-        quad = {"value": npos * wl.n_z / qs, "unit": UNIT, "probes": npos,
-                "multislice_ops": qsteps, "sample": f"{npos} seeded probes of the same scan"}
+        # the other configurations, timed the same way, each in its own precision
+        extras = []
+        for name, prec in EXTRA_CONFIGS:
+            if args.no_extra or name == args.workload:
+                continue
+            w2 = sp.WORKLOADS[name]()
+            r2 = time_workload(g, ctx, w2, prec, 3, 2, stream, 1, dev)
+            ni2 = g.count_beams(w2.n, w2.cell, w2.lam, w2.f, w2.alpha)
+            no2 = g.count_beams(w2.n, w2.cell, w2.lam, w2.f, w2.beta)
+            t2 = {k: v["ms"] for k, v in r2["prof"].items()}
+            d2 = max(t2, key=t2.get)
+            e = {"workload": w2.name, "precision": prec, "n": w2.n, "n_z": w2.n_z, "f": w2.f,
+                 "n_in": ni2, "n_out": no2, "scan": [w2.scan[0], w2.scan[1]],
+                 "value": w2.n_scan * w2.n_z / (r2["ms_total"] / 3 / 1e3), "unit": UNIT,
+                 "ms_per_step": r2["ms_total"] / 3, "steps": 3, "warmup": 2,
+                 "clocks": r2["clocks"],
+                 "roofline": _roofline(d2, w2, ni2, no2, r2["prof"], 1, peaks, tpk, r2["clocks"]),
+                 "kernels": _shares(r2["prof"], 1)}
+            if name in ref_samples:
+                e["accuracy"] = sampled_eps(g, ctx, w2, name, prec, ref_samples[name], stream)
+            extras.append(e)
+            del r2
+            torch.cuda.empty_cache()
+        out["other_configs"] = extras
 
-    # elastic by-products (Sec. IV D) of the same S-matrix: ADF (60 mrad inner) and the
-    # incoherent bright field with the EELS aperture, plus the exit-plane cost of the build
-    elastic = None
-    if rank == 0 and not args.no_elastic:
-        elastic = elastic_run(g, ctx, wl, vdev, stream, args.precision)
+        # the conventional algorithm on the same GPU, seeded probe sample, per pixel-slice
+        if not args.no_quadratic:
+            rng = np.random.default_rng(16)
+            npos = min(args.quad_probes, wl.n_scan)
+            flat = rng.choice(wl.n_scan, size=npos, replace=False)
+            pos = [(int(i // wl.scan[0]), int(i % wl.scan[0])) for i in flat]
+            g.quadratic_reference_map_for(ctx, wl, positions=pos[:1], stream=stream)
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            _, qsteps = g.quadratic_reference_map_for(ctx, wl, positions=pos, stream=stream)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            qs = q0.elapsed_time(q1) / 1e3
+            out["gpu_quadratic"] = {"value": npos * wl.n_z / qs, "unit": UNIT, "probes": npos,
+                                    "multislice_ops": qsteps,
+                                    "sample": f"{npos} seeded probes of the same scan"}
+        if not args.no_elastic:
+            vdev = torch.from_numpy(wl.vproj).cuda()
+            out["elastic"] = elastic_run(g, ctx, wl, vdev, stream, precision)
+            del vdev
+        torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel (CUDA-event times of every launch in the timed region).
-    # Tensor peak: the measured burst figure when the sampled clocks show the GPU at its
-    # maximum SM clock with no power cap during the timed region, else the sustained one
-    # (measured under the power cap at a lower clock).
-    peaks = _peaks()
-    unthrottled = bool(clk) and "sw_power_cap" not in clk["reasons"] and \
-        clk["sm_mhz"] >= 0.97 * clk["sm_max_mhz"]
-    bf16_peak = peaks["bf16_tflops"] if unthrottled else peaks["bf16_tflops_sustained"]
-    bf16_src = ("measured bf16 burst (clocks at max, no power cap)" if unthrottled
-                else "measured bf16 sustained")
-    alg = _algorithmic(wl, n_in, n_out, prof, args.steps)
-    tot = {k: v["ms"] for k, v in prof.items()}
-    dom = max(tot, key=tot.get) if tot else None
-    roof = None
-    if dom is not None:
-        launches = prof[dom]["launches"]
-        avg_s = prof[dom]["ms"] / launches / 1e3
-        per_step = launches / args.steps          # launches of this kernel in one step
-        if dom in alg and alg[dom][0] == "hbm":
-            # per step = per launch x launches per step, for bytes and time alike
-            bytes_launch = alg[dom][1] / per_step
-            achieved = bytes_launch / avg_s / 1e9
-            waves = n_out if "adjoint" in dom else n_in
-            roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": measured_traffic(dom, wl.n, waves),
-                    "algorithmic_bytes": bytes_launch,
-                    "peak_source": "measured" if "fallback" not in peaks else "fallback"}
-        elif "bf16x3" in dom:
-            useful = contraction_flops(wl, n_in, n_out, dom)
-            # the tensor pipe runs three BF16 products per real product (hi*hi, hi*lo, lo*hi)
-            peak = bf16_peak
-            achieved = 3 * useful / per_step / avg_s / 1e12
-            roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "useful_tflops": useful / per_step / avg_s / 1e12,
-                    "peak_source": bf16_src}
-        elif "tf32" in dom:
-            flops = contraction_flops(wl, n_in, n_out, dom)
-            # TF32 dense = 1.1 / 2.25 of BF16 (nominal)
-            peak = bf16_peak * TF32_PER_BF16
-            achieved = flops / per_step / avg_s / 1e12
-            roof = {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": measured_traffic(dom, wl.n, "batch"),
-                    "peak_source": bf16_src + " x nominal tf32/bf16 (1.1/2.25)"}
-        else:
-            flops = contraction_flops(wl, n_in, n_out, dom)
-            mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-            peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
-            achieved = flops / per_step / avg_s / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
-    # every multislice kernel against the HBM bound (the dominant one is in roofline) and
-    # against the FP32 ALU bound: per wave and slice the row pass runs two N-point FFTs on
-    # N rows and one complex multiply per pixel (10 N^2 log2 N + 6 N^2 flop), the column
-    # pass two N-point FFTs on the N/2 band columns and the propagator multiply
-    # (5 N^2 log2 N + 3 N^2 flop)
-    mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES * 2 * mhz * 1e6
-    lg = math.log2(wl.n)
-    nn = float(wl.n) ** 2
-    # (the last row pass of each sweep stops after the inverse FFT and the multiply)
-    row_full, row_last = 10 * nn * lg + 6 * nn, 5 * nn * lg + 6 * nn
-    col = 5 * nn * lg + 3 * nn
-    fft = {"row_pass": n_in * ((wl.n_z - 1) * row_full + row_last),
-           "row_pass_adjoint": n_out * ((wl.n_z - 1) * row_full + row_last),
-           "col_pass": n_in * (wl.n_z - 1) * col,
-           "col_pass_adjoint": n_out * (wl.n_z - 1) * col}
-    hbm = {}
-    for k in alg:
-        if k not in prof or prof[k]["ms"] <= 0:
-            continue
-        sec = prof[k]["ms"] / args.steps / 1e3
-        hbm[k] = {"achieved_gbs": alg[k][1] / sec / 1e9,
-                  "frac": alg[k][1] / sec / 1e9 / peaks["hbm_gbs"],
-                  "fft_tflops": fft[k] / sec / 1e12,
-                  "fp32_frac": fft[k] / sec / fp32_peak}
-    share = {k: {"launches": prof[k]["launches"], "ms_per_step": prof[k]["ms"] / args.steps,
-                 "share": prof[k]["ms"] / max(sum(tot.values()), 1e-9)} for k in prof}
-    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"tf32": "tf32", "bf16x3": "bf16x3"}.get(args.precision, "f32"), "data": "synthetic",
-        "config": {"workload": wl.name, "n": wl.n, "n_z": wl.n_z, "f": wl.f, "n_in": n_in,
-                   "n_out": n_out, "scan": [wl.scan[0], wl.scan[1]], "n_types": wl.n_types,
-                   "precision": args.precision, "association": args.association,
-                   "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (S_in alone is "
-                         f"{wl.n_z * n_in * (wl.n // 2) ** 2 * 8 / 1e9:.1f} GB)"},
+        "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+        "config": workload_config(wl, n_in, n_out, precision, args.association, world),
         "e2e": {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": roof,
-        "multislice_hbm": hbm,
-        "kernels": share,
+                "d2h_bytes_per_step": int(d2h), "steps": k_e2e},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "timing": "value: steps between CUDA events on the launch stream, no per-kernel "
+                  "instrumentation; kernel shares and the roofline from one more step with "
+                  "events around every launch",
         "clocks": clk,
-        "gpu_quadratic": quad,
-        "accuracy": acc,
-        "elastic": elastic,
     }
+    line.update(out)
     return line
 
 
@@ -643,10 +893,12 @@ def load_workload(args):
 
 
 def _request_arrays(req, g, precision):
+    # sin_checkpoint -1: the server keeps only checkpoints of S_in for requests whose
+    # S-matrices would take more than half of its budget
     return g.make_request(req["vproj"], req["cell"], req["lam"], req["sigma"], req["dz"], req["f"],
                           req["alpha"], req["H"], req["site_slice"], req["win_x0"], req["win_y0"],
                           req["site_x"], req["site_y"], req["scan"], req["beta"],
-                          precision=precision)
+                          precision=precision, sin_checkpoint=-1)
 
 
 def _predicted_service_s(req, g):
@@ -672,7 +924,24 @@ def _predicted_service_s(req, g):
 
 def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4):
     """Seeded Poisson stream of mixed map requests through the map server."""
-    accept = lambda req: g.request_footprint(_request_arrays(req, g, precision)[0]) <= budget
+    redrawn = []
+
+    def footprint(req):
+        # the server's own rule: S_in checkpointed every ceil(sqrt(2 n_z)) slices when
+        # storing every depth would take more than half of the budget
+        r, _ = _request_arrays(req, g, precision)
+        r.sin_checkpoint = 0
+        whole = g.request_footprint(r)
+        if whole <= budget // 2:
+            return whole, 0
+        r.sin_checkpoint = max(2, math.ceil(math.sqrt(2.0 * req["n_z"])))
+        return g.request_footprint(r), r.sin_checkpoint
+
+    def accept(req):
+        ok = footprint(req)[0] <= budget
+        if not ok:
+            redrawn.append((req["n"], req["n_z"], req["f"]))
+        return ok
     stream = sp.serving_stream(n_requests, seed=seed, accept=accept)
     pred = [_predicted_service_s(r, g) for r in stream]
     srv = g.Server(0, hbm_budget=budget, slots=slots)
@@ -698,43 +967,67 @@ def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4):
             time.sleep(delay)
         r, keep = _request_arrays(req, g, precision)
         ids.append(srv.submit(r, keep, req["n_types"], req["scan"]))
+    errors = []
     for i in ids:
-        srv.wait(i)
+        try:
+            srv.wait(i)
+        except g.EelsError as e:
+            errors.append(str(e)[:120])
     st = srv.stats()
     srv.close()
+    fps = [footprint(req) for req in stream]
     return {"requests": n_requests, "slots": slots, "hbm_budget_gb": budget / 2 ** 30,
+            "largest_footprint_gb": max(f for f, _ in fps) / 2 ** 30,
+            "checkpointed_requests": sum(1 for _, k in fps if k),
+            "errors": errors[:4],
             "precision": precision, "offered_load": load, "mean_interarrival_s": mean_gap,
             "model_scale": scale,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
             "mean_wait_ms": st["mean_wait_ms"], "makespan_s": st["makespan_s"],
             "pixel_slices_per_s": st["pixel_slices_per_s"], "completed": st["completed"],
             "failed": st["failed"], "peak_gb": st["peak_bytes"] / 2 ** 30,
+            "redrawn_over_budget": len(redrawn), "redrawn_shapes": redrawn[:16],
             "stream": "seeded (4) mixed rocksalt requests: grids 256^2-1024^2, 20-120 slices, "
                       "1-6 channels, f 2-4, scans 16^2-64^2; Poisson arrivals at the offered "
                       "load of a work model calibrated on three requests run alone; draws over "
-                      "the budget redrawn"}
+                      "the budget redrawn; tiles of 4 slices / depths interleaved over the "
+                      "slots' issue tokens"}
 
 
 def reference_arm(args, rank, world):
+    """The oracle arm: the FP64 conventional algorithm on the host cores, each step one
+    bounded sample of the same workload (its rate extrapolated by the exact multislice
+    count), plus the complete map of the small 128^2 case timed without extrapolation."""
     if rank != 0:
         return None
-    wl = sp.WORKLOADS[args.workload]()
-    vals = []
-    for _ in range(args.warmup):
-        cpu_oracle_rate(args.workload)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        rate, cores, sample = cpu_oracle_rate(args.workload)
-        vals.append(rate)
-    wall = time.perf_counter() - t0
+    from oracle import multislice as ms
+    smp = OracleSampler(args.workload)
+    wl = smp.wl
+    precision = args.precision or CONFIG_PRECISION.get(args.workload, "bf16x3")
+    n_in = ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)[0].size
+    n_out = ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)[0].size
+    try:
+        for _ in range(args.warmup):
+            smp.sample()
+        vals, ops = [], 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            rate, sample, rec = smp.sample()
+            vals.append(rate)
+            ops += rec["ops"]
+        total = time.perf_counter() - t0
+    finally:
+        smp.close()
     value = float(np.mean(vals))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": wl.n_scan * wl.n_z / value * 1e3,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl.name, "precision": "fp64 oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "config": workload_config(wl, n_in, n_out, precision, args.association, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": smp.procs, "kind": "oracle",
+                             "sample": sample + f"; each step one such sample ({ops} ops over "
+                                                f"{args.steps} steps, {total:.1f} s)"},
+            "full_small_map": cpu_oracle_full("rocksalt_small"),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -746,8 +1039,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sp.WORKLOADS))
-    ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
-    ap.add_argument("--quad-probes", type=int, default=8)
+    ap.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16x3"],
+                    help="contraction precision (default: the one the workload's configuration names)")
+    ap.add_argument("--quad-probes", type=int, default=4)
     ap.add_argument("--association", default="auto",
                     choices=["auto", "transition_first", "probe_first"])
     ap.add_argument("--sout-scheme", default="stream", choices=["stream", "recompute", "inverse"],
@@ -755,18 +1049,19 @@ def main():
     ap.add_argument("--s2-study", action="store_true",
                     help="print the S_out scheme thickness study instead of the bench line")
     ap.add_argument("--no-elastic", action="store_true", help="skip the ADF / BF images")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other configurations")
     ap.add_argument("--phonons", type=int, default=0,
                     help="print the frozen-phonon average over this many configurations")
     ap.add_argument("--crop-study", action="store_true",
                     help="print the crop-window study (Sec. IV B) instead of the bench line")
     ap.add_argument("--no-quadratic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-eps", action="store_true", help="skip the FP32 accuracy reference")
-    ap.add_argument("--no-serving", action="store_true", help="skip the short serving stream")
+    ap.add_argument("--no-eps", action="store_true", help="skip the FP64-oracle accuracy samples")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request stream")
     ap.add_argument("--serving", action="store_true",
                     help="only run the mixed request stream through the map server")
     ap.add_argument("--serving-requests", type=int, default=64)
-    ap.add_argument("--serving-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serving-budget-gb", type=float, default=240.0)
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--max-slices", type=int, default=0,
                     help="keep only the first K slices (smaller device footprint for profiling)")
@@ -778,11 +1073,16 @@ def main():
         if line is not None:
             print(json.dumps(line))
         return
-    # the CPU sample forks worker processes: run it before the first CUDA call
-    cpu = None
+    # the host work forks worker processes: run it before the first CUDA call
+    cpu, ref_samples = None, {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(args.workload)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        rate, cores, sample, rec = cpu_oracle_rate(args.workload)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               **rec}
+    if rank == 0 and not args.no_eps and not args.max_slices:
+        names = [args.workload] + [n for n, _ in EXTRA_CONFIGS
+                                   if not args.no_extra and n != args.workload]
+        ref_samples = oracle_samples([n for n in names if n in ORACLE_SAMPLES])
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
@@ -793,7 +1093,7 @@ def main():
         import paper_1908_07628_gb300 as g
         torch.cuda.init()
         res = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
-                          args.serving_slots, args.precision)
+                          args.serving_slots, args.precision or "bf16x3")
         print(json.dumps({"metric": "EELS map serving p99 latency", "value": res["p99_ms"],
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
@@ -805,7 +1105,7 @@ def main():
         build.build()
         import paper_1908_07628_gb300 as g
         res = phonon_run(g, g.Context(0), torch.cuda.current_stream(), args.phonons,
-                         args.precision)
+                         args.precision or "tf32")
         print(json.dumps({"study": "frozen-phonon average", "metric": METRIC, "data": "synthetic",
                           **res}))
         return
@@ -828,11 +1128,14 @@ def main():
         print(json.dumps({"study": "S_out schemes (Sec. III listing, Sec. IV C inverse multislice)",
                           "data": "synthetic", **res}))
         return
-    line = gpu_arm(args, rank, world)
+    line = gpu_arm(args, rank, world, ref_samples)
     line["cpu_baseline"] = cpu
     if rank == 0 and not args.no_serving:
+        import torch
         import paper_1908_07628_gb300 as g
-        line["serving"] = serving_run(g, 12, 48 << 30, 3, args.precision)
+        torch.cuda.empty_cache()
+        line["serving"] = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
+                                      args.serving_slots, "bf16x3")
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -47,7 +47,8 @@ typedef enum {
   EELS_ERR_UNSUPPORTED = 2,  /* grid size or option not built into this library */
   EELS_ERR_OOM = 3,          /* device allocation failed */
   EELS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
-  EELS_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+  EELS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  EELS_ERR_CANCELLED = 6     /* a map server request was cancelled or passed its deadline */
 } eels_status;
 
 /* Arithmetic of the inelastic contraction (Eq. SHn0 and the |.|^2 scan sum).
@@ -55,8 +56,10 @@ typedef enum {
  * always accumulated in FP64. */
 typedef enum {
   EELS_PREC_FP32 = 0,        /* FP32 CUDA-core complex GEMMs */
-  EELS_PREC_TF32 = 1,        /* tcgen05 TF32 tensor cores, FP32 accumulate */
-  EELS_PREC_BF16X3 = 2       /* tcgen05 BF16 hi+lo split (3 products), FP32 accumulate */
+  EELS_PREC_TF32 = 1,        /* tcgen05 TF32 hi+lo split (3 products), FP32 accumulate: about
+                                21 significant bits per operand, the FP32-class tensor path */
+  EELS_PREC_BF16X3 = 2       /* tcgen05 BF16 hi+lo split (3 products), FP32 accumulate: about
+                                16 significant bits per operand, the reduced-precision path */
 } eels_precision;
 
 typedef struct eels_ctx eels_ctx;
@@ -215,6 +218,11 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  * M_n = S_out^H diag(H_n) S_in and then M_n a(R) (the paper's order);
  * EELS_ASSOC_PROBE_FIRST forms Y = S_in a(R) once per site (the elastic wave inside the
  * window) and then S_out^H (H_n . Y) per channel.  Both give the same map up to rounding.
+ * EELS_ASSOC_MODEL picks, per call, the grouping with fewer complex products over the
+ * call's sites (transition first: T (n_out w^2 n_in + n_out n_in n_R) per site; probe
+ * first: n_R n_in w^2 + T n_out w^2 n_R), without timing anything, so that the choice and
+ * with it the rounding of the map never depend on what else runs on the device (the map
+ * server uses it).
  *
  * EELS_OPT_SHARD_COUNT (G >= 1, default 1) and EELS_OPT_SHARD_INDEX (0 <= g < G,
  * default 0) restrict eels_inelastic_map to one shard of the detector beams: beam d
@@ -230,6 +238,7 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 #define EELS_ASSOC_AUTO 0
 #define EELS_ASSOC_TRANSITION_FIRST 1
 #define EELS_ASSOC_PROBE_FIRST 2
+#define EELS_ASSOC_MODEL 3
 #define EELS_OPT_SHARD_COUNT 2
 #define EELS_OPT_SHARD_INDEX 3
 /* EELS_OPT_SOUT_SCHEME selects how eels_inelastic_map brings the detector-side
@@ -249,6 +258,28 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  * surface (one more depth of n_in N/2 x N/2 planes and one more half slice step), which
  * eels_elastic_images needs. */
 #define EELS_OPT_EXIT_PLANE 5
+/* EELS_OPT_SIN_CHECKPOINT (K >= 0, default 0): a build with K >= 2 does not store S_in at
+ * every depth; it keeps the probe waves at every K-th depth (ceil(n_z / K) copies of n_in
+ * N x N/2 row spectra) and eels_inelastic_map recomputes S_in one segment of K depths at a
+ * time as the backward sweep reaches it (one more forward pass: n_z n_in more beam-steps).
+ * The map is the same bit for bit up to the order of the FP64 sums.  K near sqrt(2 n_z)
+ * minimises the memory, about (2 n_z / K + K) instead of n_z planes of (N/2)^2 per probe
+ * beam; this runs specimens whose S_in does not fit in HBM.  Needs the stream S_out scheme
+ * (EELS_ERR_UNSUPPORTED otherwise); eels_smatrix_copy_depth returns EELS_ERR_UNSUPPORTED
+ * for such a handle.  0 and 1 store every depth. */
+#define EELS_OPT_SIN_CHECKPOINT 8
+/* EELS_OPT_BATCH_SITES (>= 0, default 0): at most this many sites of one slice are
+ * contracted per batch of tensor-core launches; 0 sizes the batch by a 3 GiB budget for
+ * the operand buffers.  The map does not depend on it (up to FP64 summation order);
+ * smaller batches use less device memory and more launches. */
+#define EELS_OPT_BATCH_SITES 6
+/* EELS_OPT_WAIT_TEST (>= 0, default 0), for failure-detection tests only: a value v > 0
+ * limits every pipeline wait of the tensor-core kernels to 1000 v clock cycles and makes
+ * their TMA producers issue no load, so that the consumers' bounded waits run out with
+ * nothing in flight; each kernel then records the timeout, frees its tensor memory and
+ * returns, and eels_inelastic_map returns EELS_ERR_TIMEOUT.  The context stays usable;
+ * set 0 to return to normal operation. */
+#define EELS_OPT_WAIT_TEST 7
 #define EELS_OPT_SOUT_SCHEME 4
 #define EELS_SOUT_STREAM 0
 #define EELS_SOUT_RECOMPUTE 1
@@ -269,19 +300,23 @@ int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
 #define EELS_STATIC_SCRATCH_BYTES (64ull << 20)
 
 /* S_in build that allocates nothing (the paper has no counterpart: this is a
- * deployment variant of eels_build_smatrix).  For callers that cannot call
- * cudaMalloc -- code running while a CUDA graph is being captured, plug-ins whose
- * host application owns or has reserved the device memory, real-time loops that
- * must not risk an allocation failure -- it writes what eels_build_smatrix stores,
- * S_in(i) for every depth as complex64 [n_z][n_in][N/2][N/2] scaled by N, into the
- * caller's device buffer s_in (s_in_bytes long), and keeps all its work arrays in
- * one static device array of EELS_STATIC_SCRATCH_BYTES that every GPU loading
- * the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.  vproj may be host or device memory; it takes no
- * context and reports errors as a status plus text in err (err_cap bytes).
- * *n_in_out receives the number of probe beams.
+ * deployment variant of eels_build_smatrix).  Some callers cannot call cudaMalloc:
+ * plug-ins whose host application owns (or has reserved) all of the device memory,
+ * and real-time acquisition loops that must not take the time of, or risk the
+ * failure of, an allocation in the middle of a run.  This call writes what
+ * eels_build_smatrix stores, S_in(i) for every depth as complex64
+ * [n_z][n_in][N/2][N/2] scaled by N, into the caller's device buffer s_in
+ * (s_in_bytes long), and keeps all its work arrays in one static device array of
+ * EELS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * vproj may be host or device memory (a host vproj is copied slice by slice into
+ * the static array); it takes no context and reports errors as a status plus text
+ * in err (err_cap bytes).  *n_in_out receives the number of probe beams once every
+ * check has passed; a rejected call leaves it untouched.
  * - The first call on a device looks up the device address of the static array
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress) and keeps it for the process; make that first call
+ *   before any stream capture.  The address is not looked up again, so a call
+ *   after cudaDeviceReset on that device is undefined.
  * - Every call on a device shares the array and leaves its contents behind;
  *   calls whose GPU work overlaps (different streams or threads) race.
  * - Waves are processed in chunks sized to the static array (at N = 512 about 30
@@ -296,12 +331,19 @@ eels_status eels_build_smatrix_static(const eels_specimen* spec, const eels_opti
 /* ---------------------------------------------------------------------------
  * Map server (not in the paper: a serving loop around the calls above).
  * A request is one complete map: S-matrix build plus inelastic map.  Requests are
- * queued in arrival order and admitted when one of `slots` workers is free and the
- * request's device footprint (eels_request_footprint) fits in what is left of
- * hbm_budget bytes; admission is first-fit in arrival order, and a request bypassed
- * eight times stops further bypassing until it is admitted.  Each worker has its own
- * context and non-blocking stream, so admitted requests overlap on the device; a
- * request's S_in stays resident until its map is done.
+ * queued in arrival order and admitted as soon as the request's device footprint
+ * (eels_request_footprint) fits in what is left of hbm_budget bytes; admission is
+ * first-fit in arrival order, and a request bypassed eight times stops further
+ * bypassing until it is admitted.  Each admitted request runs on its own context and
+ * non-blocking stream, and its S_in stays resident until its map is done.
+ * Work is issued in tiles of four slices of the build or four depths of the map (the
+ * backward S_out step and the contraction of the sites at those depths).  `slots` issue
+ * tokens gate the device: a request holds a token while it issues one tile, lets that
+ * tile finish, hands the token to the request that has waited longest and queues again,
+ * so the tiles of admitted requests interleave and overlap on the device.  A cancelled
+ * request, or one past its deadline, is dropped at its next tile boundary (or before
+ * admission) with EELS_ERR_CANCELLED and its memory released.  Contexts of the server
+ * use EELS_ASSOC_MODEL, so a request's map does not depend on the other requests.
  * --------------------------------------------------------------------------- */
 typedef struct eels_server eels_server;
 
@@ -312,35 +354,63 @@ typedef struct {
   eels_scan scan;
   double beta;
   int precision;             /* eels_precision */
+  double deadline_s;         /* > 0: dropped once this many seconds have passed since
+                                submission (checked at tile boundaries); 0: no deadline */
+  int sin_checkpoint;        /* as EELS_OPT_SIN_CHECKPOINT; -1: the server picks
+                                K = ceil(sqrt(2 n_z)) if storing every depth would take more
+                                than half its budget, else stores every depth */
 } eels_request;
 
 typedef struct {
-  int64_t submitted, completed, failed;
+  int64_t submitted, completed, failed, cancelled;
   double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> done latency of completed requests */
-  double mean_wait_ms;                      /* submit -> admission */
+  double mean_wait_ms;                      /* submit -> first tile issued */
   double makespan_s;                        /* first submit -> last completion */
   double pixel_slices_per_s;                /* sum of n_scan n_z of completed requests / makespan */
   int64_t peak_bytes;                       /* largest sum of admitted footprints */
 } eels_server_stats;
 
-/* Device bytes the server reserves for a request while it runs: transmissions, S_in,
- * the larger of the forward and backward work arrays, a 4 GiB cap for contraction
- * buffers and the transition potentials.  -1 for invalid sizes. */
+/* Progress of one request; times in seconds since the server was created, -1 if the
+ * event has not happened. */
+typedef struct {
+  int done;                 /* 1 once finished (completed, failed or cancelled) */
+  int status;               /* eels_status once done */
+  double t_submit, t_admit, t_first_tile, t_done;
+  int tiles;                /* tiles issued */
+  int64_t footprint;        /* device bytes reserved while admitted */
+} eels_request_info;
+
+/* Device bytes the server reserves for a request while it runs: transmissions, S_in (or
+ * its checkpoints when sin_checkpoint >= 2), the larger of the build's work arrays and the
+ * map's (backward work arrays, one S_out depth, a 4 GiB cap for contraction buffers, the
+ * transition potentials and, with checkpoints, the forward work arrays and one segment of
+ * S_in).  sin_checkpoint = -1 counts as 0.  -1 for invalid sizes. */
 int64_t eels_request_footprint(const eels_request* req);
-/* Start `slots` workers on `device` sharing an HBM budget of hbm_budget bytes. */
+/* Start a server on `device` with `slots` issue tokens and an HBM budget of hbm_budget
+ * bytes. */
 eels_status eels_server_create(int device, int64_t hbm_budget, int slots, eels_server** out);
 /* Queue a request; its input arrays are BORROWED until eels_server_wait has returned
  * for it.  *id identifies it.  EELS_ERR_OOM if its footprint exceeds the whole budget,
- * EELS_ERR_ARG for device inputs or invalid sizes. */
+ * EELS_ERR_ARG for device inputs, a negative deadline or invalid sizes. */
 eels_status eels_server_submit(eels_server* sv, const eels_request* req, int64_t* id);
+/* Ask for request id to be dropped: at once if it is not admitted yet, else at its next
+ * tile boundary.  Its wait then returns EELS_ERR_CANCELLED.  No effect once it is done. */
+eels_status eels_server_cancel(eels_server* sv, int64_t id);
 /* Block until request id is done (timeout_s <= 0: no limit) and copy its FP64 map
  * [n_types][n_sy][n_sx] to host map_out (may be NULL); *latency_s (if non-NULL) gets its
  * submit-to-completion time.  Returns the request's own status, or EELS_ERR_TIMEOUT. */
 eels_status eels_server_wait(eels_server* sv, int64_t id, double* map_out, double timeout_s,
                              double* latency_s);
+eels_status eels_server_request_info(eels_server* sv, int64_t id, eels_request_info* out);
 eels_status eels_server_stats_get(eels_server* sv, eels_server_stats* out);
-/* Stop the workers after their current requests; requests not yet admitted are dropped. */
+/* Stop admitting; requests not yet admitted are dropped, admitted ones run to completion. */
 void eels_server_destroy(eels_server* sv);
+
+/* Measured FP32 FMA rate of device `device` (flop/s, 2 per FMA), the denominator of
+ * the CUDA-core ALU roofline (no counterpart in the paper: a measurement aid).  Runs
+ * one launch of independent FMA chains, `iters` FMAs per chain, timed with CUDA
+ * events on the legacy default stream (about 1e9 iters take a few hundred ms). */
+eels_status eels_fp32_fma_rate(int device, int iters, double* flops_per_s);
 
 /* Number of f-lattice beams with lambda |k| <= angle (Sec. III, pi alpha^2 L^2 / f^2). */
 int eels_count_beams(int n, double cell, double lambda, int f, double angle);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libstemeels.so")
 
 EELS_PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2}
 _STATUS = {0: "EELS_OK", 1: "EELS_ERR_ARG", 2: "EELS_ERR_UNSUPPORTED", 3: "EELS_ERR_OOM",
-           4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT"}
+           4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT", 6: "EELS_ERR_CANCELLED"}
 
 
 class EelsError(RuntimeError):
@@ -50,12 +50,19 @@ class Scan(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("spec", Specimen), ("optics", Optics), ("tr", Transitions), ("scan", Scan),
-                ("beta", C.c_double), ("precision", C.c_int)]
+                ("beta", C.c_double), ("precision", C.c_int), ("deadline_s", C.c_double),
+                ("sin_checkpoint", C.c_int)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_first_tile", C.c_double), ("t_done", C.c_double),
+                ("tiles", C.c_int), ("footprint", C.c_int64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
-                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("cancelled", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_ms", C.c_double), ("mean_wait_ms", C.c_double), ("makespan_s", C.c_double),
                 ("pixel_slices_per_s", C.c_double), ("peak_bytes", C.c_int64)]
 
@@ -75,6 +82,7 @@ EXPORTS = {
                                     C.POINTER(C.c_int)]),
     "eels_smatrix_beams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "eels_smatrix_copy_depth": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "eels_fp32_fma_rate": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "eels_inelastic_map": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Transitions),
                                      C.POINTER(Scan), C.c_double, C.c_int, C.c_void_p, C.c_int,
                                      C.c_void_p]),
@@ -102,6 +110,8 @@ EXPORTS = {
     "eels_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_double,
                                    C.POINTER(C.c_double)]),
     "eels_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "eels_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "eels_server_request_info": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestInfo)]),
     "eels_server_destroy": (None, [C.c_void_p]),
     "eels_count_beams": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double]),
     "eels_memory_model": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
@@ -190,7 +200,7 @@ class Context:
             msg = self._lib.eels_last_error(self._h)
             raise EelsError(st, f"{what}: {msg.decode() if msg else ''}")
 
-    ASSOCIATIONS = {"auto": 0, "transition_first": 1, "probe_first": 2}
+    ASSOCIATIONS = {"auto": 0, "transition_first": 1, "probe_first": 2, "model": 3}
 
     def set_association(self, how: str = "auto"):
         """Grouping of the tensor-core contraction (EELS_OPT_ASSOCIATION)."""
@@ -205,6 +215,22 @@ class Context:
     def set_exit_plane(self, on: bool = True):
         """Builds also keep S_in at the exit surface (EELS_OPT_EXIT_PLANE), for elastic_images."""
         self._check(self._lib.eels_set_option(self._h, 5, 1 if on else 0), "set_option")
+
+    def set_batch_sites(self, cap: int = 0):
+        """At most `cap` sites of a slice per tensor-core contraction batch
+        (EELS_OPT_BATCH_SITES); 0 sizes batches by the operand memory budget."""
+        self._check(self._lib.eels_set_option(self._h, 6, int(cap)), "set_option")
+
+    def set_sin_checkpoint(self, k: int = 0):
+        """Builds keep the probe waves every k slices instead of S_in at every depth
+        (EELS_OPT_SIN_CHECKPOINT); maps recompute S_in segment by segment.  0: off."""
+        self._check(self._lib.eels_set_option(self._h, 8, int(k)), "set_option")
+
+    def set_wait_test(self, kcycles: int = 0):
+        """Failure-detection test mode (EELS_OPT_WAIT_TEST): kcycles > 0 limits the
+        tensor-core pipeline waits to 1000 * kcycles clock cycles and withholds every TMA
+        load, so the waits run out; 0 restores normal operation."""
+        self._check(self._lib.eels_set_option(self._h, 7, int(kcycles)), "set_option")
 
     def elastic_images(self, sm, scan, detectors, out=None, stream=None):
         """Elastic images [n_det][n_sy][n_sx] (FP64) for detectors [(inner, outer), ...]
@@ -418,6 +444,15 @@ def build_smatrix_static(vproj, cell, lam, sigma, dz, f, alpha, out, stream=None
     return int(n_in.value)
 
 
+def fp32_fma_rate(device=0, iters=1 << 20) -> float:
+    """eels_fp32_fma_rate: measured FP32 FMA flop/s of the device."""
+    out = C.c_double(0.0)
+    st = load().eels_fp32_fma_rate(int(device), int(iters), C.byref(out))
+    if st != 0:
+        raise EelsError(st, "eels_fp32_fma_rate")
+    return out.value
+
+
 def count_beams(n, cell, lam, f, angle) -> int:
     return int(load().eels_count_beams(int(n), float(cell), float(lam), int(f), float(angle)))
 
@@ -458,7 +493,7 @@ def quadratic_reference_map_for(ctx: Context, wl, positions=None, stream=None):
 # -- map server --------------------------------------------------------------------------
 
 def make_request(vproj, cell, lam, sigma, dz, f, alpha, H, site_slice, win_x0, win_y0, site_x,
-                 site_y, scan, beta, precision="tf32"):
+                 site_y, scan, beta, precision="tf32", deadline_s=0.0, sin_checkpoint=0):
     """eels_request over host arrays; returns (request, keepalive)."""
     v, on_dev, vkeep = _ptr(vproj, np.float32)
     if on_dev:
@@ -468,7 +503,7 @@ def make_request(vproj, cell, lam, sigma, dz, f, alpha, H, site_slice, win_x0, w
     req = Request(Specimen(n, n_z, float(cell), v, 0),
                   Optics(float(lam), float(sigma), float(dz), int(f), float(alpha)), tr,
                   Scan(*[int(x) for x in scan[:2]], *[float(x) for x in scan[2:]]), float(beta),
-                  EELS_PREC[precision])
+                  EELS_PREC[precision], float(deadline_s), int(sin_checkpoint))
     return req, (vkeep, tkeep)
 
 
@@ -506,9 +541,25 @@ class Server:
         if st == 5:
             raise EelsError(st, "eels_server_wait timed out")
         self._keep.pop(rid, None)
+        if st == 6:
+            raise EelsError(st, f"request {rid} cancelled")
         if st != 0:
             raise EelsError(st, f"request {rid} failed")
         return out, float(lat.value)
+
+    def cancel(self, rid: int):
+        """eels_server_cancel: drop the request before admission or at its next tile."""
+        st = self._lib.eels_server_cancel(self._h, int(rid))
+        if st != 0:
+            raise EelsError(st, "eels_server_cancel")
+
+    def info(self, rid: int) -> dict:
+        """eels_server_request_info: status, times (s since server start) and tiles."""
+        r = RequestInfo()
+        st = self._lib.eels_server_request_info(self._h, int(rid), C.byref(r))
+        if st != 0:
+            raise EelsError(st, "eels_server_request_info")
+        return {name: getattr(r, name) for name, _ in RequestInfo._fields_}
 
     def stats(self) -> dict:
         s = ServerStats()

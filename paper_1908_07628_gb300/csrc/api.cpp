@@ -23,6 +23,13 @@ struct eels_ctx {
   int shard_count = 1, shard_index = 0;   // detector-beam shard of eels_inelastic_map
   int sout_scheme = EELS_SOUT_STREAM;     // how S_out reaches each depth
   bool keep_exit = false;                 // builds also store S_in at the exit surface
+  int sin_ckpt = 0;                       // builds checkpoint the waves every K slices (K >= 2)
+  int batch_sites = 0;                    // cap on sites per contraction batch (0: by memory)
+  int wait_test = 0;                      // failure test: short pipeline waits, loads withheld
+  // called between tiles of work (after each slice of a build, after each depth of a map);
+  // a non-zero return abandons the call with EELS_ERR_CANCELLED (the map server's gate)
+  eels::TileHook hook = nullptr;
+  void* hook_user = nullptr;
   // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
   std::map<std::vector<int64_t>, int> assoc_cache;
   std::string err;
@@ -45,6 +52,10 @@ struct eels_smatrix {
   float2* ptab = nullptr;      // [n/2][n/2] box order, forward propagator / N^2
   float2* s_in = nullptr;      // [n_z][n_in][n/2][n/2]
   float2* s_exit = nullptr;    // [n_in][n/2][n/2] exit surface, N Dec(psi_j(n_z)), or null
+  // checkpointed form (s_in null): the probe waves psi_j(cK) in row-spectrum form,
+  // [ceil(n_z/K)][n_in][n][n/2]; S_in of a segment of K depths is recomputed from them
+  int ckpt_k = 0;
+  float2* ckpt = nullptr;
   cudaStream_t st = nullptr;   // stream the handle's memory is ordered on
 };
 
@@ -200,7 +211,17 @@ eels_status build_slices(eels_ctx* ctx, const eels_specimen* spec, const eels_op
   return EELS_OK;
 }
 
+// Tile boundary: true if the hook asks to abandon the call.
+bool cancelled(eels_ctx* ctx, int phase, int done, int total) {
+  return ctx->hook && ctx->hook(ctx->hook_user, phase, done, total) != 0;
+}
+
 }  // namespace
+
+void eels::set_tile_hook(eels_ctx* ctx, TileHook fn, void* user) {
+  ctx->hook = fn;
+  ctx->hook_user = user;
+}
 
 extern "C" {
 
@@ -238,7 +259,7 @@ const char* eels_last_error(const eels_ctx* ctx) { return ctx ? ctx->err.c_str()
 eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
   if (!ctx) return EELS_ERR_ARG;
   if (option == EELS_OPT_ASSOCIATION) {
-    if (value < EELS_ASSOC_AUTO || value > EELS_ASSOC_PROBE_FIRST)
+    if (value < EELS_ASSOC_AUTO || value > EELS_ASSOC_MODEL)
       return fail(ctx, EELS_ERR_ARG, "unknown association");
     ctx->assoc = value;
     return EELS_OK;
@@ -249,9 +270,24 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     ctx->sout_scheme = value;
     return EELS_OK;
   }
+  if (option == EELS_OPT_SIN_CHECKPOINT) {
+    if (value < 0) return fail(ctx, EELS_ERR_ARG, "checkpoint interval must be >= 0");
+    ctx->sin_ckpt = value >= 2 ? value : 0;
+    return EELS_OK;
+  }
   if (option == EELS_OPT_EXIT_PLANE) {
     if (value != 0 && value != 1) return fail(ctx, EELS_ERR_ARG, "exit plane option is 0 or 1");
     ctx->keep_exit = value == 1;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_BATCH_SITES) {
+    if (value < 0) return fail(ctx, EELS_ERR_ARG, "batch site cap must be >= 0");
+    ctx->batch_sites = value;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_WAIT_TEST) {
+    if (value < 0) return fail(ctx, EELS_ERR_ARG, "wait test value must be >= 0");
+    ctx->wait_test = value;
     return EELS_OK;
   }
   if (option == EELS_OPT_SHARD_COUNT) {
@@ -356,6 +392,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
   sm->cell = spec->cell; sm->lam = op->lambda; sm->sigma = op->sigma; sm->dz = op->dz;
   sm->alpha = op->alpha;
   sm->bp = bp; sm->bq = bq;
+  sm->ckpt_k = ctx->sin_ckpt;
   auto bail = [&](eels_status code) { eels_smatrix_free(sm); return code; };
   const int64_t plane = (int64_t)nh * nh;
   cudaError_t e;
@@ -364,9 +401,15 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
   if ((e = cudaMallocAsync((void**)&sm->t, sizeof(float2) * (size_t)n_z * n * n, st)) !=
           cudaSuccess ||
       (e = cudaMallocAsync((void**)&sm->ptab, sizeof(float2) * (size_t)plane, st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void**)&sm->s_in,
-                           sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane), st)) !=
-          cudaSuccess ||
+      (!ctx->sin_ckpt &&
+       (e = cudaMallocAsync((void**)&sm->s_in,
+                            sizeof(float2) * (size_t)(n_z * (int64_t)n_in * plane), st)) !=
+           cudaSuccess) ||
+      (ctx->sin_ckpt &&
+       (e = cudaMallocAsync((void**)&sm->ckpt,
+                            sizeof(float2) * (size_t)((n_z + ctx->sin_ckpt - 1) / ctx->sin_ckpt) *
+                                n_in * n * nh,
+                            st)) != cudaSuccess) ||
       (ctx->keep_exit &&
        (e = cudaMallocAsync((void**)&sm->s_exit, sizeof(float2) * (size_t)(n_in * plane), st)) !=
            cudaSuccess))
@@ -389,12 +432,20 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
     if ((e = eels::launch_init_plane_waves(W.p, n, n_in, dpx.p, dpy.p, damp.p, tw, st)) != cudaSuccess)
       return bail(cuda_fail(ctx, e, "init plane waves"));
   }
+  const int K = sm->ckpt_k;
   for (int i = 0; i < n_z; ++i) {
     const bool last = (i == n_z - 1) && !sm->s_exit;   // the exit plane needs one more half step
+    if (K && i % K == 0) {   // checkpoint psi_j(i), the row pass input of slice i
+      e = cudaMemcpyAsync(sm->ckpt + (int64_t)(i / K) * n_in * n * nh, W.p,
+                          sizeof(float2) * (size_t)n_in * n * nh, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "checkpoint"));
+    }
+    if (K && last) break;    // nothing after the last checkpoint is stored
     {
       Prof pr(ctx, "row_pass", st);
-      e = launch_row_pass(n, n_in, W.p, Phi.p, sm->t + (int64_t)i * n * n, 0, 1,
-                          sm->s_in + (int64_t)i * n_in * plane, n_in, plane, last ? 0 : 1, tw, st);
+      e = launch_row_pass(n, n_in, W.p, Phi.p, sm->t + (int64_t)i * n * n, 0, K ? 0 : 1,
+                          K ? nullptr : sm->s_in + (int64_t)i * n_in * plane, K ? 0 : n_in, plane,
+                          last ? 0 : 1, tw, st);
     }
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "row pass"));
     if (!last) {
@@ -403,6 +454,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
                           st);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "column pass"));
     }
+    if (cancelled(ctx, 0, i + 1, n_z)) return bail(fail(ctx, EELS_ERR_CANCELLED, "cancelled"));
   }
   if (sm->s_exit) {   // psi_j(n_z) = F^-1 P F (t psi_j(n_z - 1)) is in W: store N Dec of it
     Prof pr(ctx, "row_pass_store", st);
@@ -420,6 +472,7 @@ void eels_smatrix_free(eels_smatrix* sm) {
   if (sm->t) cudaFreeAsync(sm->t, sm->st);
   if (sm->ptab) cudaFreeAsync(sm->ptab, sm->st);
   if (sm->s_exit) cudaFreeAsync(sm->s_exit, sm->st);
+  if (sm->ckpt) cudaFreeAsync(sm->ckpt, sm->st);
   if (sm->s_in) cudaFreeAsync(sm->s_in, sm->st);
   delete sm;
   (void)cudaGetLastError();   // a void call leaves no error for the caller's next call
@@ -441,6 +494,7 @@ eels_status eels_smatrix_beams(const eels_smatrix* sm, int32_t* p, int32_t* q) {
 
 eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* dst, void* stream) {
   if (!sm || !dst || depth < 0 || depth >= sm->n_z) return EELS_ERR_ARG;
+  if (!sm->s_in) return EELS_ERR_UNSUPPORTED;   // checkpointed: S_in is not stored
   eels_ctx* ctx = sm->ctx;
   EELS_CK(enter(ctx));
   const int64_t per = (int64_t)sm->bp.size() * (sm->n / 2) * (sm->n / 2);
@@ -615,6 +669,16 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   EELS_CK(Phi.alloc((size_t)n_out * n * nh, st));
   EELS_CK(dmap.alloc((size_t)n_map, st));
   EELS_CK(cudaMemsetAsync(dmap.p, 0, sizeof(double) * n_map, st));
+  // checkpointed S-matrix: forward work arrays and one segment of K depths of S_in
+  const int K = sm->ckpt_k;
+  DevBuf<float2> Wf, Phif, seg;
+  if (sm->ckpt) {
+    if (ctx->sout_scheme != EELS_SOUT_STREAM)
+      return fail(ctx, EELS_ERR_UNSUPPORTED, "a checkpointed S-matrix needs the stream scheme");
+    EELS_CK(Wf.alloc((size_t)n_in * n * nh, st));
+    EELS_CK(Phif.alloc((size_t)n_in * n * nh, st));
+    EELS_CK(seg.alloc((size_t)K * n_in * plane, st));
+  }
 
   // M buffer: a batch of transitions, at most ~1 GiB
   const int64_t m_stride = (int64_t)n_out * n_in;
@@ -635,6 +699,19 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   // AUTO: measured once per shape (both groupings timed on the first occupied slice)
   const std::vector<int64_t> shape_key = {tc_prec, n, n_out, n_in, w, nr_cap, T};
   int chosen = ctx->assoc;
+  if (chosen == EELS_ASSOC_MODEL) {
+    // complex products of each grouping over the map's sites (Eq. SHn0 applied to the
+    // probes): the smaller one, with no timing, so the choice never depends on load
+    double c_tr = 0, c_pr = 0;
+    const double P2 = (double)w * w;
+    for (int s = 0; s < S; ++s) {
+      const double nr = (double)L.xcnt[s] * L.ycnt[s];
+      if (nr == 0) continue;
+      c_tr += T * ((double)n_out * P2 * n_in + (double)n_out * n_in * nr);
+      c_pr += nr * n_in * P2 + T * (double)n_out * P2 * nr;
+    }
+    chosen = c_pr <= c_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
+  }
   if (chosen == EELS_ASSOC_AUTO) {
     auto it = ctx->assoc_cache.find(shape_key);
     if (it != ctx->assoc_cache.end()) chosen = it->second;
@@ -642,8 +719,10 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   bool tune = tc && chosen == EELS_ASSOC_AUTO;
   const bool need_tr = tune || chosen == EELS_ASSOC_TRANSITION_FIRST;
   const bool need_pr = tune || chosen == EELS_ASSOC_PROBE_FIRST;
+  const int vbytes = tc ? eels::tc_value_bytes(tc_prec) : 4;   // operand bytes per value
+  const int vf = vbytes / 4;                                      // ... in floats
   const int64_t per_site =
-      4 * ((int64_t)n_out * k1p +
+      vbytes * ((int64_t)n_out * k1p +
            (need_pr ? (int64_t)nr_cap * k2p + (int64_t)k1p * k2p + (int64_t)T * 2 * nr_cap * k1p
                     : 0) +
            (need_tr ? (int64_t)T * 2 * n_in * k1p + (int64_t)T * n_out * k2p +
@@ -651,8 +730,9 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
                     : 0));
   int max_sites = 0;
   for (int i = 0; i < n_z; ++i) max_sites = std::max(max_sites, (int)slice_sites[i].size());
-  const int sb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(max_sites, 1),
-                                                             ((int64_t)3 << 30) / per_site));
+  int sb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(max_sites, 1),
+                                                       ((int64_t)3 << 30) / per_site));
+  if (ctx->batch_sites > 0) sb = std::min(sb, ctx->batch_sites);
   DevBuf<float> A1, B1, M1, B2, AY, BY, BV;
   DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus, daby, dnvy, dnry;
   DevBuf<double> dscratch;
@@ -698,21 +778,21 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     EELS_CK(dbb2.upload(bb2.data(), bb2.size(), st));
     EELS_CK(dstatus.alloc(1, st));
     EELS_CK(cudaMemsetAsync(dstatus.p, 0, sizeof(int), st));
-    EELS_CK(A1.alloc((size_t)sb * n_out * k1p, st));
+    EELS_CK(A1.alloc((size_t)vf * sb * n_out * k1p, st));
     if (need_pr) {
       std::vector<int> aby(sb), nvy(sb, k1p);
       for (int q = 0; q < sb; ++q) aby[q] = q;
       EELS_CK(daby.upload(aby.data(), aby.size(), st));
       EELS_CK(dnvy.upload(nvy.data(), nvy.size(), st));
       EELS_CK(dnry.upload(nr_all.data(), nr_all.size(), st));
-      EELS_CK(AY.alloc((size_t)sb * nr_cap * k2p, st));
-      EELS_CK(BY.alloc((size_t)sb * k1p * k2p, st));
-      EELS_CK(BV.alloc((size_t)sb * T * 2 * nr_cap * k1p, st));
+      EELS_CK(AY.alloc((size_t)vf * sb * nr_cap * k2p, st));
+      EELS_CK(BY.alloc((size_t)vf * sb * k1p * k2p, st));
+      EELS_CK(BV.alloc((size_t)vf * sb * T * 2 * nr_cap * k1p, st));
     }
     if (need_tr) {
-      EELS_CK(B1.alloc((size_t)sb * T * 2 * n_in * k1p, st));
-      EELS_CK(M1.alloc((size_t)sb * T * n_out * k2p, st));
-      EELS_CK(B2.alloc((size_t)sb * 2 * nr_cap * k2p, st));
+      EELS_CK(B1.alloc((size_t)vf * sb * T * 2 * n_in * k1p, st));
+      EELS_CK(M1.alloc((size_t)vf * sb * T * n_out * k2p, st));
+      EELS_CK(B2.alloc((size_t)vf * sb * 2 * nr_cap * k2p, st));
     }
     if (tune) EELS_CK(dscratch.alloc((size_t)n_map, st));
   }
@@ -723,7 +803,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   }
   eels::WindowLists wl{dxoff.p, dxcnt.p, dxlist.p, dyoff.p, dycnt.p, dylist.p, L.max_nr};
   // tensor-core contraction of slice i with one grouping, accumulated into `map`
-  auto contract_slice = [&](const float2* Sin, int i, int pf, double* map) -> eels_status {
+  // assoc: EELS_ASSOC_TRANSITION_FIRST or EELS_ASSOC_PROBE_FIRST
+  auto contract_slice = [&](const float2* Sin, int i, int assoc, double* map) -> eels_status {
     for (int q0 = site_off[i]; q0 < site_off[i + 1]; q0 += sb) {
       const int ns = std::min(sb, site_off[i + 1] - q0);
       eels::TcBatch b{};
@@ -744,10 +825,12 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;
       b.a_batch2 = dab2.p; b.b_batch2 = dbb2.p; b.n_valid2 = dnv2.p + (int64_t)q0 * T;
       b.map = map; b.status = dstatus.p;
+      b.wait_cycles = ctx->wait_test > 0 ? 1000LL * ctx->wait_test : 0;
+      b.withhold = ctx->wait_test > 0 ? 1 : 0;
       b.AY = AY.p; b.BY = BY.p; b.BV = BV.p; b.a_batch_y = daby.p; b.n_valid_y = dnvy.p;
       b.m_valid_y = dnry.p ? dnry.p + q0 : nullptr;
       const bool bf = tc_prec == EELS_TC_BF16X3;
-      if (pf) {
+      if (assoc == EELS_ASSOC_PROBE_FIRST) {
         {
           Prof pr(ctx, "tc_gather_y", st);
           EELS_CK(eels::tc_gather_y(b, st));
@@ -779,38 +862,38 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   };
   // contraction of depth i (S_out(i) in Sout) into the map
   auto contract_depth = [&](int i) -> eels_status {
-    const float2* Sin = sm->s_in + (int64_t)i * n_in * plane;
+    const float2* Sin = sm->ckpt ? seg.p + (int64_t)(i % K) * n_in * plane
+                                 : sm->s_in + (int64_t)i * n_in * plane;
     if (tc && site_off[i + 1] > site_off[i]) {
-      int pf = chosen == EELS_ASSOC_PROBE_FIRST ? 1 : 0;
       if (tune) {
-        // warm both paths on the scratch map, then time each once and keep the faster
+        // warm both groupings on the scratch map, then time each once and keep the
+        // faster; the timed transition-first run accumulates this slice into the map
+        constexpr int kGroupings = 2;
+        const int order[kGroupings] = {EELS_ASSOC_TRANSITION_FIRST, EELS_ASSOC_PROBE_FIRST};
         EELS_CK(cudaMemsetAsync(dscratch.p, 0, sizeof(double) * n_map, st));
-        eels_status r1 = contract_slice(Sin, i, 1, dscratch.p);
-        if (r1 != EELS_OK) return r1;
-        if ((r1 = contract_slice(Sin, i, 0, dscratch.p)) != EELS_OK) return r1;
-        cudaEvent_t e0, e1, e2;
-        EELS_CK(cudaEventCreate(&e0));
-        EELS_CK(cudaEventCreate(&e1));
-        EELS_CK(cudaEventCreate(&e2));
-        EELS_CK(cudaEventRecord(e0, st));
-        if ((r1 = contract_slice(Sin, i, 0, dmap.p)) != EELS_OK) return r1;
-        EELS_CK(cudaEventRecord(e1, st));
-        if ((r1 = contract_slice(Sin, i, 1, dscratch.p)) != EELS_OK) return r1;
-        EELS_CK(cudaEventRecord(e2, st));
-        EELS_CK(cudaEventSynchronize(e2));
-        float t_tr = 0.f, t_pr = 0.f;
-        cudaEventElapsedTime(&t_tr, e0, e1);
-        cudaEventElapsedTime(&t_pr, e1, e2);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaEventDestroy(e2);
-        // the timed transition-first run accumulated this slice into the map; the
-        // remaining slices use the faster grouping
-        chosen = t_pr < t_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
+        eels_status r1 = EELS_OK;
+        for (int a : order)
+          if ((r1 = contract_slice(Sin, i, a, dscratch.p)) != EELS_OK) return r1;
+        cudaEvent_t ev[kGroupings + 1];
+        for (auto& e : ev) EELS_CK(cudaEventCreate(&e));
+        EELS_CK(cudaEventRecord(ev[0], st));
+        for (int k = 0; k < kGroupings; ++k) {
+          if ((r1 = contract_slice(Sin, i, order[k], k == 0 ? dmap.p : dscratch.p)) != EELS_OK)
+            return r1;
+          EELS_CK(cudaEventRecord(ev[k + 1], st));
+        }
+        EELS_CK(cudaEventSynchronize(ev[kGroupings]));
+        float best = 0.f;
+        for (int k = 0; k < kGroupings; ++k) {
+          float t = 0.f;
+          cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+          if (k == 0 || t < best) { best = t; chosen = order[k]; }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
         ctx->assoc_cache[shape_key] = chosen;
         tune = false;
       } else {
-        eels_status r1 = contract_slice(Sin, i, pf, dmap.p);
+        eels_status r1 = contract_slice(Sin, i, chosen, dmap.p);
         if (r1 != EELS_OK) return r1;
       }
     }
@@ -831,6 +914,12 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   };
   const auto t_of = [&](int i) { return sm->t + (int64_t)i * n * n; };
   const auto has_work = [&](int i) { return slice_off[i + 1] > slice_off[i]; };
+  // some depth of the segment whose top depth is i holds transitions
+  const auto has_work_to = [&](int i) {
+    for (int j = i / K * K; j <= i; ++j)
+      if (has_work(j)) return true;
+    return false;
+  };
   // one backward slice step of the detector waves in `from` (row-spectrum form):
   // conj(t_i), x-FFT, then y-FFT, conj(P), inverse y-FFT into `to`
   auto back_step = [&](float2* from, float2* tmp, int i) -> eels_status {
@@ -851,10 +940,34 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     return EELS_OK;
   };
 
+  // checkpointed S-matrix: S_in(cK .. i) of the segment whose top depth is i, recomputed
+  // from the checkpoint psi_j(cK) with the same row and column passes as the build
+  auto recompute_segment = [&](int i) -> eels_status {
+    const int c0 = i / K * K;
+    EELS_CK(cudaMemcpyAsync(Wf.p, sm->ckpt + (int64_t)(i / K) * n_in * n * nh,
+                            sizeof(float2) * (size_t)n_in * n * nh, cudaMemcpyDeviceToDevice, st));
+    for (int j = c0; j <= i; ++j) {
+      {
+        Prof pr(ctx, "row_pass_recompute", st);
+        EELS_CK(launch_row_pass(n, n_in, Wf.p, Phif.p, t_of(j), 0, 1,
+                                seg.p + (int64_t)(j - c0) * n_in * plane, n_in, plane,
+                                j < i ? 1 : 0, tw, st));
+      }
+      if (j < i) {
+        Prof pr(ctx, "col_pass_recompute", st);
+        EELS_CK(launch_col_pass(n, n_in, Phif.p, Wf.p, sm->ptab, 0, 0, nullptr, nullptr, nullptr,
+                                0.0, tw, st));
+      }
+    }
+    return EELS_OK;
+  };
+
   eels_status rs = EELS_OK;
   if (ctx->sout_scheme == EELS_SOUT_STREAM) {
     // S_out streamed backwards once (Alg. 2 with the slice loop run from the exit)
     for (int i = n_z - 1; i >= 0; --i) {
+      if (sm->ckpt && (i == n_z - 1 || (i + 1) % K == 0) && has_work_to(i))
+        if ((rs = recompute_segment(i)) != EELS_OK) return rs;
       // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
       {
         Prof pr(ctx, "row_pass_adjoint", st);
@@ -867,6 +980,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         EELS_CK(launch_col_pass(n, n_out, Phi.p, W.p, sm->ptab, 1, 0, nullptr, nullptr, nullptr,
                                 0.0, tw, st));
       }
+      if (cancelled(ctx, 1, n_z - i, n_z)) return fail(ctx, EELS_ERR_CANCELLED, "cancelled");
     }
   } else if (ctx->sout_scheme == EELS_SOUT_RECOMPUTE) {
     // Alg. 2 as listed: S_2 recalculated from the exit surface for every depth
@@ -880,6 +994,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         if ((rs = back_step(W.p, Phi.p, j)) != EELS_OK) return rs;
       if ((rs = store_sout(W.p, i)) != EELS_OK) return rs;
       if ((rs = contract_depth(i)) != EELS_OK) return rs;
+      if (cancelled(ctx, 1, i + 1, n_z)) return fail(ctx, EELS_ERR_CANCELLED, "cancelled");
     }
   } else {
     // Sec. IV C: S_2 carried back to depth 0 once, then retreated one slice per depth
@@ -900,6 +1015,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         if ((rs = store_sout(cur, i)) != EELS_OK) return rs;
         if ((rs = contract_depth(i)) != EELS_OK) return rs;
       }
+      if (cancelled(ctx, 1, i + 1, n_z)) return fail(ctx, EELS_ERR_CANCELLED, "cancelled");
       if (i + 1 == n_z) break;
       {
         Prof pr(ctx, "col_pass_inverse", st);

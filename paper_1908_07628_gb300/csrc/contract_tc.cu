@@ -11,11 +11,11 @@
 //           B2[2r]   = conj(a_r),  B2[2r+1] = i conj(a_r)  -> C2 = (Re, Im) of V[d][r]
 //           map[type][R_r] += sum_d C2[d][2r]^2 + C2[d][2r+1]^2     (fused epilogue)
 //
-// Two operand precisions:
-//   TF32    every operand rounded to the nearest TF32; kind::tf32 MMAs.
-//   BF16x3  every operand x stored as hi = bf16(x) and lo = bf16(x - hi) (two
-//           planes); each product is lo*hi + hi*lo + hi*hi with kind::f16 MMAs into
-//           the same FP32 accumulator (the lo*lo term is below FP32 resolution).
+// Two operand precisions, both a hi + lo split of every operand x into two planes,
+// each product being lo*hi + hi*lo + hi*hi into the same FP32 accumulator (the lo*lo
+// term is below the resolution the split keeps):
+//   TF32    hi = tf32(x), lo = tf32(x - hi), kind::tf32 MMAs (about 21 significant bits);
+//   BF16x3  hi = bf16(x), lo = bf16(x - hi), kind::f16 MMAs (about 16 significant bits).
 // Operands are gathered into K-padded buffers [batch][plane][rows][K] and streamed
 // by TMA (128-byte swizzle) through an mbarrier pipeline.  Every GEMM runs one persistent,
 // warp-specialised kernel with a double-buffered TMEM accumulator (k_tc_gemm_ws).
@@ -41,7 +41,7 @@ template <>
 struct Prec<EELS_TC_TF32> {
   using T = float;
   static constexpr int BK = 32;         // 128 bytes of K per row
-  static constexpr int PLANES = 1;
+  static constexpr int PLANES = 2;      // hi, lo
   static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   static constexpr uint32_t IDESC = tc::idesc_tf32(BM, BN);
 };
@@ -62,12 +62,21 @@ struct Tile {
   static constexpr int STAGE_BYTES = P::PLANES * (A_BYTES + B_BYTES);
 };
 
+// plane pl of the TF32 hi + lo split of x (0: hi = x rounded; 1: lo = x - hi rounded)
+__device__ __forceinline__ float tf32_part(float x, int pl) {
+  const float h = tc::to_tf32(x);
+  return pl == 0 ? h : tc::to_tf32(x - h);
+}
+
 // store the pair (a, b) at element e of a row, in every plane of the precision
 template <int PREC>
 __device__ __forceinline__ void put2(void* base, int64_t plane_stride, int64_t e, float a, float b) {
   if constexpr (PREC == EELS_TC_TF32) {
-    reinterpret_cast<float2*>(static_cast<float*>(base) + e)[0] =
-        make_float2(tc::to_tf32(a), tc::to_tf32(b));
+    float* p = static_cast<float*>(base);
+    const float ah = tc::to_tf32(a), bh = tc::to_tf32(b);
+    reinterpret_cast<float2*>(p + e)[0] = make_float2(ah, bh);
+    reinterpret_cast<float2*>(p + plane_stride + e)[0] =
+        make_float2(tc::to_tf32(a - ah), tc::to_tf32(b - bh));
   } else {
     __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
     const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
@@ -92,11 +101,17 @@ __device__ __forceinline__ uint32_t bf16_pair(__nv_bfloat16 lo, __nv_bfloat16 hi
 template <int PREC>
 __device__ __forceinline__ void put16(void* base, int64_t plane_stride, int64_t e, const float* v) {
   if constexpr (PREC == EELS_TC_TF32) {
-    float4* d = reinterpret_cast<float4*>(static_cast<float*>(base) + e);
+    float* p = static_cast<float*>(base);
+    float4* dh = reinterpret_cast<float4*>(p + e);
+    float4* dl = reinterpret_cast<float4*>(p + plane_stride + e);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      d[q] = make_float4(tc::to_tf32(v[4 * q]), tc::to_tf32(v[4 * q + 1]), tc::to_tf32(v[4 * q + 2]),
-                         tc::to_tf32(v[4 * q + 3]));
+    for (int q = 0; q < 4; ++q) {
+      const float4 h = make_float4(tc::to_tf32(v[4 * q]), tc::to_tf32(v[4 * q + 1]),
+                                   tc::to_tf32(v[4 * q + 2]), tc::to_tf32(v[4 * q + 3]));
+      dh[q] = h;
+      dl[q] = make_float4(tc::to_tf32(v[4 * q] - h.x), tc::to_tf32(v[4 * q + 1] - h.y),
+                          tc::to_tf32(v[4 * q + 2] - h.z), tc::to_tf32(v[4 * q + 3] - h.w));
+    }
   } else {
     __align__(16) __nv_bfloat16 hi[16], lo[16];
 #pragma unroll
@@ -123,6 +138,8 @@ struct EpiStore {
   int cols;
 };
 
+// |.|^2 epilogue (GEMM 2, GEMM-V): map[type][R] += sum over rows of C[row][2R]^2 +
+// C[row][2R+1]^2.
 struct EpiAbs2 {
   const int* z_site;
   const int* z_type;
@@ -166,30 +183,31 @@ struct EpiSpread {
 namespace ws {
 constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter, one per column half
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int CW = 32;                          // GEMM-Y epilogue chunk (columns, 128 B)
-constexpr int TILE = 2 * BM * CW * 4;           // one chunk of one channel: 256 rows x 128 B,
-                                                // 128-byte swizzled, stored by one TMA box
-constexpr int TG = 1;                           // channels staged at once per column half
-// BF16 GEMM-Y stages one plane of a 32-column chunk at a time: 256 rows x 64 bytes
-// (32 BF16 values), 64-byte swizzled, 16 KB per column half.
-constexpr int TILE_BF16 = 2 * BM * 32 * 2;
-// TF32 stages are 48 KB (4, or 3 beside the GEMM-Y staging); BF16 hi + lo stages are
-// 96 KB (2, also beside the smaller BF16 GEMM-Y staging: 2 x 96 + 2 x 16 KB).
+// GEMM-Y stages one plane of a chunk of columns at a time: 256 rows x 64 bytes (16 TF32
+// or 32 BF16 values), 64-byte swizzled, 16 KB per column half.
+constexpr int STG_ROW = 64;
+constexpr int TILE_STG = 2 * BM * STG_ROW;
+// Stages hold both planes of a 128-byte K block of A and B: 96 KB, two of them (also
+// beside the GEMM-Y staging: 2 x 96 + 2 x 16 KB).
 template <int MODE, int PREC>
 __host__ __device__ constexpr int stages() {
-  return PREC == EELS_TC_TF32 ? (MODE == 2 ? 3 : 4) : 2;
+  return 2;
 }
 template <int MODE, int PREC>
 __host__ __device__ constexpr size_t staging_half() {
-  return MODE != 2 ? 0 : PREC == EELS_TC_TF32 ? (size_t)TG * TILE : (size_t)TILE_BF16;
+  return MODE != 2 ? 0 : (size_t)TILE_STG;
 }
 template <int MODE, int PREC>
 __host__ __device__ constexpr size_t smem() {
   return (size_t)stages<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + 2 * staging_half<MODE, PREC>() +
          1024 + 256;
 }
-static_assert(smem<2, EELS_TC_BF16X3>() + (BN / 2) * 4 + 16 <= 232448,
-              "BF16 GEMM-Y stages and staging exceed the shared memory of a CTA");
+static_assert(smem<2, EELS_TC_BF16X3>() + (BN / 2) * 4 + 16 <= 232448 &&
+                  smem<2, EELS_TC_TF32>() + (BN / 2) * 4 + 16 <= 232448,
+              "GEMM-Y stages and staging exceed the shared memory of a CTA");
+static_assert(smem<1, EELS_TC_BF16X3>() + 4 * (BN / 2) * 4 + 16 <= 232448 &&
+                  smem<1, EELS_TC_TF32>() + 4 * (BN / 2) * 4 + 16 <= 232448,
+              "BF16 GEMM stages and the |.|^2 partial sums exceed the shared memory of a CTA");
 }  // namespace ws
 
 // named barrier of the four epilogue warps of one column half (ids 1 and 2)
@@ -203,12 +221,15 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
              const __grid_constant__ CUtensorMap tv, int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
              const int* __restrict__ a_batch, const int* __restrict__ b_batch,
              const int* __restrict__ n_valid, const int* __restrict__ m_valid, EpiStore es,
-             EpiAbs2 ea, EpiSpread ey, int* __restrict__ status) {
+             EpiAbs2 ea, EpiSpread ey, int* __restrict__ status, long long wait_cycles,
+             int withhold) {
   using P = Prec<PREC>;
   using TL = Tile<PREC>;
   constexpr int S = ws::stages<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ float red[BN / 2];
+  // |.|^2 partial sums of the column pairs, one row per TMEM lane quarter; summed in a
+  // fixed order so that a map does not depend on warp scheduling
+  __shared__ float red[MODE == 1 ? 4 : 1][BN / 2];   // only the |.|^2 epilogue uses it
   __shared__ int abort_flag;
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -274,13 +295,15 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      // withhold (failure-detection test): issue no load at all, so that the consumers'
+      // bounded waits run out while nothing is in flight
+      for (int t = blockIdx.x; t < tiles && ok && !withhold; t += gridDim.x) {
         int z, n0, m0;
         if (!decode(t, z, n0, m0)) continue;
         const int ab = a_batch[z], bb = b_batch[z];
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const int s = it % S;
-          if (it >= S && !(ok = tc::mbar_wait(empty + s, ((it / S) - 1) & 1))) break;
+          if (it >= S && !(ok = tc::mbar_wait(empty + s, ((it / S) - 1) & 1, wait_cycles))) break;
           uint8_t* st = sm + s * TL::STAGE_BYTES;
           tc::mbar_arrive_expect_tx(full + s, TL::STAGE_BYTES);
 #pragma unroll
@@ -301,25 +324,27 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
         int z, n0, m0;
         if (!decode(t, z, n0, m0)) continue;
         const int b = i & 1;
-        if (i >= 2 && !(ok = tc::mbar_wait(acc_empty + b, ((i >> 1) - 1) & 1))) break;
+        if (i >= 2 && !(ok = tc::mbar_wait(acc_empty + b, ((i >> 1) - 1) & 1, wait_cycles))) break;
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(b * BN);
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const int s = it % S;
-          if (!(ok = tc::mbar_wait(full + s, (it / S) & 1))) break;
+          if (!(ok = tc::mbar_wait(full + s, (it / S) & 1, wait_cycles))) break;
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(sm + s * TL::STAGE_BYTES);
           const uint32_t sb = sa + PL * TL::A_BYTES;
-          // each MMA consumes 32 bytes of K: 8 TF32 or 16 BF16 elements
+          // each MMA consumes 32 bytes of K: 8 TF32 or 16 BF16 elements; the small
+          // products first (lo*hi, hi*lo), then hi*hi
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+            const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
+            const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
             if constexpr (PREC == EELS_TC_TF32) {
-              tc::mma_tf32(d, tc::desc_sw128(sa + kk * 32), tc::desc_sw128(sb + kk * 32),
-                           P::IDESC, acc);
+              tc::mma_tf32(d, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
+              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
+              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
             } else {
-              const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
-              const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
               tc::mma_f16(d, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
               tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
               tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
@@ -346,7 +371,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
       int z, n0, m0;
       if (!decode(t, z, n0, m0)) continue;
       const int b = i & 1;
-      if (!tc::mbar_wait(acc_full + b, (i >> 1) & 1)) atomicOr(&abort_flag, 1);
+      if (!tc::mbar_wait(acc_full + b, (i >> 1) & 1, wait_cycles)) atomicOr(&abort_flag, 1);
       epi_sync(half);
       if (abort_flag) {
         ok = false;
@@ -364,22 +389,25 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           if (row < es.rows && col < es.cols)
             put16<PREC>(es.out, es.plane_stride, rbase + col, v);
         }
-      } else if constexpr (MODE == 2 && PREC == EELS_TC_BF16X3) {
-        // chunks of 32 columns (16 pixels): each thread forms its two rows (H_t Y and
-        // -i H_t Y) and writes them, hi plane then lo plane, into the half's staging tile
-        // (64-byte rows, 64-byte swizzle); one thread of the half stores each plane with one
-        // TMA box, and the tile is rewritten only after that store has read it
+      } else if constexpr (MODE == 2) {
+        // chunks of CC columns (CC / 2 pixels; 64 bytes of one plane per operand row): each
+        // thread forms its two rows (H_t Y and -i H_t Y) and writes them, hi plane then lo
+        // plane, into the half's staging tile (64-byte rows, 64-byte swizzle); one thread of
+        // the half stores each plane with one TMA box, and the tile is rewritten only after
+        // that store has read it
+        constexpr int CC = ws::STG_ROW / (int)sizeof(typename P::T);   // 16 TF32, 32 BF16
+        constexpr int PX = CC / 2;
         const int site = ey.slot_site[z];
         const int rr = 2 * (q4 * 32 + lane);
-        for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += 32) {
+        for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += CC) {
           for (int t0 = 0; t0 < ey.n_types; ++t0) {
-            float v[32];
+            float v[CC];
             tc::tmem_ld16(trow + c, v);
-            tc::tmem_ld16(trow + c + 16, v + 16);
+            if constexpr (CC == 32) tc::tmem_ld16(trow + c + 16, v + 16);
             const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0) * ey.P;
-            float2 y[16];
+            float2 y[PX];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < PX; ++k) {
               const int pp = (n0 + c) / 2 + k;
               const float2 h = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
               y[k] = cmul(h, make_float2(v[2 * k], v[2 * k + 1]));
@@ -387,22 +415,35 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             for (int pl = 0; pl < 2; ++pl) {
               if (te == 0) tc::bulk_wait_read();
               epi_sync(half);
-              uint8_t* r0 = stg_h + (size_t)rr * 64;
-              uint8_t* r1 = r0 + 64;
+              uint8_t* r0 = stg_h + (size_t)rr * ws::STG_ROW;
+              uint8_t* r1 = r0 + ws::STG_ROW;
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {   // 16-byte chunk q: pixels 4q .. 4q + 3
-                uint32_t a[4], b[4];
+              for (int q = 0; q < 4; ++q) {   // 16-byte chunk q of the 64-byte row
+                uint4 a, b;
+                if constexpr (PREC == EELS_TC_TF32) {   // pixels 2q, 2q + 1
+                  const float2 u0 = y[2 * q], u1 = y[2 * q + 1];
+                  a = make_uint4(__float_as_uint(tf32_part(u0.x, pl)),
+                                 __float_as_uint(tf32_part(u0.y, pl)),
+                                 __float_as_uint(tf32_part(u1.x, pl)),
+                                 __float_as_uint(tf32_part(u1.y, pl)));
+                  b = make_uint4(__float_as_uint(tf32_part(u0.y, pl)),
+                                 __float_as_uint(tf32_part(-u0.x, pl)),
+                                 __float_as_uint(tf32_part(u1.y, pl)),
+                                 __float_as_uint(tf32_part(-u1.x, pl)));
+                } else {                                 // pixels 4q .. 4q + 3
+                  uint32_t wa[4], wb[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const float2 u = y[4 * q + e];
-                  a[e] = bf16_pair(bf16_part(u.x, pl), bf16_part(u.y, pl));
-                  b[e] = bf16_pair(bf16_part(u.y, pl), bf16_part(-u.x, pl));
+                  for (int e = 0; e < 4; ++e) {
+                    const float2 u = y[4 * q + e];
+                    wa[e] = bf16_pair(bf16_part(u.x, pl), bf16_part(u.y, pl));
+                    wb[e] = bf16_pair(bf16_part(u.y, pl), bf16_part(-u.x, pl));
+                  }
+                  a = make_uint4(wa[0], wa[1], wa[2], wa[3]);
+                  b = make_uint4(wb[0], wb[1], wb[2], wb[3]);
                 }
                 // chunk q of 64-byte row r sits at chunk q ^ ((r >> 1) & 3) (64-byte swizzle)
-                *reinterpret_cast<uint4*>(r0 + ((q ^ ((rr >> 1) & 3)) << 4)) =
-                    make_uint4(a[0], a[1], a[2], a[3]);
-                *reinterpret_cast<uint4*>(r1 + ((q ^ (((rr + 1) >> 1) & 3)) << 4)) =
-                    make_uint4(b[0], b[1], b[2], b[3]);
+                *reinterpret_cast<uint4*>(r0 + ((q ^ ((rr >> 1) & 3)) << 4)) = a;
+                *reinterpret_cast<uint4*>(r1 + ((q ^ (((rr + 1) >> 1) & 3)) << 4)) = b;
               }
               tc::fence_async_shared();
               epi_sync(half);
@@ -413,49 +454,8 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             }
           }
         }
-      } else if constexpr (MODE == 2) {
-        // chunks of 32 columns: each thread forms its two rows (H_t Y and -i H_t Y) in the
-        // half's staging tile (128-byte swizzled rows), and one thread of the half stores
-        // the tile with one TMA box; the tile is rewritten only after that store has read it
-        const int site = ey.slot_site[z];
-        const int rr = 2 * (q4 * 32 + lane);
-        for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += ws::CW) {
-          for (int t0 = 0; t0 < ey.n_types; ++t0) {
-            float v[ws::CW];
-            tc::tmem_ld16(trow + c, v);
-            tc::tmem_ld16(trow + c + 16, v + 16);
-            if (te == 0) tc::bulk_wait_read();
-            epi_sync(half);
-            const float2* Ht = ey.H + ((int64_t)site * ey.h_mul * ey.n_types + t0) * ey.P;
-            uint8_t* r0 = stg_h + (size_t)rr * (ws::CW * 4);
-            uint8_t* r1 = r0 + ws::CW * 4;
-#pragma unroll
-            for (int q = 0; q < ws::CW / 4; ++q) {
-              const int pp = (n0 + c) / 2 + 2 * q;
-              const float2 h0 = pp < ey.P ? __ldg(Ht + pp) : make_float2(0.f, 0.f);
-              const float2 h1 = pp + 1 < ey.P ? __ldg(Ht + pp + 1) : make_float2(0.f, 0.f);
-              const float2 y0 = cmul(h0, make_float2(v[4 * q], v[4 * q + 1]));
-              const float2 y1 = cmul(h1, make_float2(v[4 * q + 2], v[4 * q + 3]));
-              // 16-byte chunk q of row r sits at chunk q ^ (r & 7) (128-byte swizzle)
-              *reinterpret_cast<float4*>(r0 + ((q ^ (rr & 7)) << 4)) =
-                  make_float4(tc::to_tf32(y0.x), tc::to_tf32(y0.y), tc::to_tf32(y1.x),
-                              tc::to_tf32(y1.y));
-              *reinterpret_cast<float4*>(r1 + ((q ^ ((rr + 1) & 7)) << 4)) =
-                  make_float4(tc::to_tf32(y0.y), tc::to_tf32(-y0.x), tc::to_tf32(y1.y),
-                              tc::to_tf32(-y1.x));
-            }
-            tc::fence_async_shared();
-            epi_sync(half);
-            if (te == 0) {
-              tc::tma_store_4d(&tv, stg_h, n0 + c, 2 * m0, 0, z * ey.n_types + t0);
-              tc::bulk_commit();
-            }
-          }
-        }
       } else {
-        // this half owns red[c_lo / 2 .. c_hi / 2)
-        for (int k = c_lo / 2 + te; k < c_hi / 2; k += 128) red[k] = 0.f;
-        epi_sync(half);
+        // this half owns red[*][c_lo / 2 .. c_hi / 2); every entry is written once below
         const bool live = row < ea.rows;
         for (int c = c_lo; c < c_hi; c += 16) {
           float v[16];
@@ -480,8 +480,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
           float r1 = (b2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r2[0] : r2[1], 4);
           r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
           r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
-          if ((lane & 3) == 0)
-            atomicAdd(&red[c / 2 + (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)], r1);
+          if ((lane & 3) == 0) red[q4][c / 2 + (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)] = r1;
         }
         epi_sync(half);
         const int s = ea.z_site[z];
@@ -493,7 +492,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             const int ix = ea.xlist[ea.xoff[s] + r % nx];
             const int iy = ea.ylist[ea.yoff[s] + r / nx];
             const int64_t idx = ((int64_t)ea.z_type[z] * ea.n_sy + iy) * ea.n_sx + ix;
-            atomicAdd(ea.map + idx, (double)red[k]);
+            atomicAdd(ea.map + idx, (double)(((red[0][k] + red[1][k]) + red[2][k]) + red[3][k]));
           }
         }
         epi_sync(half);
@@ -824,7 +823,7 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
                         int gz, const int* tile_prefix, const int* a_batch, const int* b_batch,
                         const int* n_valid, const int* m_valid, const EpiStore& es,
                         const EpiAbs2& ea, const EpiSpread& ey, int* status, cudaStream_t st,
-                        int valid_tiles) {
+                        int valid_tiles, long long wait_cycles, int withhold) {
   if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
   static std::atomic<uint64_t> attr{0};
   cudaError_t e = smem_attr_once(k_tc_gemm_ws<MODE, PREC>, ws::smem<MODE, PREC>(), attr);
@@ -832,9 +831,10 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
   const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
   if (tiles <= 0) return cudaSuccess;
   const int grid = std::min(tiles, sm_count());
+  if (wait_cycles <= 0) wait_cycles = tc::kWaitCycles;   // 0: the default limit
   k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
       ta, tb, tv, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
-      status);
+      status, wait_cycles, withhold);
   return cudaGetLastError();
 }
 
@@ -852,7 +852,7 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   EpiSpread ey{};
   return launch_gemm<0, PREC>(mA1, mB1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, nullptr, b.a_batch1,
-                              b.b_batch1, b.n_valid1, nullptr, es, ea, ey, b.status, st, 0);
+                              b.b_batch1, b.n_valid1, nullptr, es, ea, ey, b.status, st, 0, b.wait_cycles, b.withhold);
 }
 
 template <int PREC>
@@ -871,7 +871,7 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   return launch_gemm<1, PREC>(mM1, mB2, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch2, b.b_batch2, b.n_valid2, nullptr, es, ea, ey, b.status,
-                              st, b.n_tiles_v);
+                              st, b.n_tiles_v, b.wait_cycles, b.withhold);
 }
 
 // Association with the probe sum first: gathers for GEMM-Y (A1 is shared with GEMM-V).
@@ -902,17 +902,17 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{};
   EpiSpread ey{b.BV, Prec<PREC>::PLANES * pstride, pstride, b.k1p, b.nr_cap, b.w * b.w,
                b.n_types, b.H, b.h_mul, b.slot_site};
-  // store map of GEMM-Y's output: BV rows (2 per probe) in boxes of 32 columns x 256 rows
-  // of one plane (TF32: 128-byte rows, 128-byte swizzle; BF16: 64-byte rows and swizzle)
+  // store map of GEMM-Y's output: BV rows (2 per probe) in boxes of 64 bytes x 256 rows
+  // of one plane (16 TF32 or 32 BF16 columns), 64-byte swizzle
   CUtensorMap mBV;
-  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, 2 * BM, 32,
-                          PREC == EELS_TC_TF32 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                               : CU_TENSOR_MAP_SWIZZLE_64B)) != cudaSuccess)
+  if ((e = make_map<PREC>(&mBV, b.BV, b.k1p, 2 * b.nr_cap, b.slots_cap * b.n_types, 2 * BM,
+                          ws::STG_ROW / (int)sizeof(typename Prec<PREC>::T),
+                          CU_TENSOR_MAP_SWIZZLE_64B)) != cudaSuccess)
     return e;
   return launch_gemm<2, PREC>(mAY, mBY, mBV, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
                               (b.nr_cap + BM - 1) / BM, b.n_sites, b.tiles_y, b.a_batch_y,
                               b.a_batch_y, b.n_valid_y, b.m_valid_y, es, ea, ey, b.status, st,
-                              b.n_tiles_y);
+                              b.n_tiles_y, b.wait_cycles, b.withhold);
 }
 
 template <int PREC>
@@ -930,7 +930,7 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   return launch_gemm<1, PREC>(mA1, mBV, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch1, b.b_batch1, b.n_valid2, nullptr, es, ea, ey, b.status,
-                              st, b.n_tiles_v);
+                              st, b.n_tiles_v, b.wait_cycles, b.withhold);
 }
 
 }  // namespace
@@ -951,6 +951,12 @@ cudaError_t tc_gemm_v(const TcBatch& b, cudaStream_t st) {
   if (b.n_sites <= 0) return cudaSuccess;
   return b.prec == EELS_TC_BF16X3 ? gemm_v_impl<EELS_TC_BF16X3>(b, st)
                                   : gemm_v_impl<EELS_TC_TF32>(b, st);
+}
+
+int tc_value_bytes(int prec) {
+  return prec == EELS_TC_BF16X3
+             ? Prec<EELS_TC_BF16X3>::PLANES * (int)sizeof(Prec<EELS_TC_BF16X3>::T)
+             : Prec<EELS_TC_TF32>::PLANES * (int)sizeof(Prec<EELS_TC_TF32>::T);
 }
 
 int tc_k_align(int prec) {

@@ -5,7 +5,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct eels_ctx;
+
 namespace eels {
+
+// Tile hook of a context: called between tiles of work with phase 0 (build: `done` of
+// `total` slices stepped) or 1 (map: `done` of `total` depths contracted), after the
+// tile's work is queued on the call's stream.  A non-zero return abandons the call with
+// EELS_ERR_CANCELLED.  The map server installs one on each of its contexts.
+typedef int (*TileHook)(void* user, int phase, int done, int total);
+void set_tile_hook(eels_ctx* ctx, TileHook fn, void* user);
 
 // True if the multislice kernels are compiled for grid side n.
 bool grid_supported(int n);
@@ -111,10 +120,11 @@ cudaError_t launch_cut_detect(int m, float2* X, int n_cut, const uint8_t* mask, 
 // Tensor-core (tcgen05) contraction of a batch of sites of one slice: gathers the
 // windowed operands, runs GEMM 1 (M = Sout^H diag(H) Sin) and GEMM 2 with the fused
 // sum_d |.|^2 epilogue into map.  All pointers are device memory.  Operand buffers
-// hold 4 bytes per value in both precisions (one TF32 plane, or BF16 hi + lo planes).
+// hold tc_value_bytes(prec) bytes per value: hi + lo planes of TF32 (8) or BF16 (4).
 #define EELS_TC_TF32 0
 #define EELS_TC_BF16X3 1
 int tc_k_align(int prec);   // K padding (elements) of the operand buffers
+int tc_value_bytes(int prec);   // bytes per operand value, both planes
 struct TcBatch {
   int prec;                               // EELS_TC_TF32 or EELS_TC_BF16X3
   const float2* Sout; const float2* Sin;  // depth planes [beam][nh][nh]
@@ -135,6 +145,8 @@ struct TcBatch {
   const int* a_batch2; const int* b_batch2; const int* n_valid2;
   double* map;
   int* status;                            // set to 1 if a bounded wait timed out
+  long long wait_cycles;                  // limit of the pipeline waits, clock cycles (0: default)
+  int withhold;                           // 1: TMA producers issue no load (failure test)
   // association with the probe sum first (GEMM-Y then per-channel GEMM-V)
   void* AY; void* BY; void* BV;           // a rows, S_in window transposed, H_t . Y rows
   const int* a_batch_y; const int* n_valid_y;   // identity map and k1p per site

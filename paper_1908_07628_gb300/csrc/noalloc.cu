@@ -1,10 +1,9 @@
 // eels_build_smatrix_static: the S_in build for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph capture,
-// plug-ins living inside a host application that owns the device memory pool
-// (or has reserved all of it), and real-time loops that must not pay for or risk
-// an allocation failure mid-run.  For them this entry point produces exactly what
+// Some callers cannot call cudaMalloc: plug-ins living inside a host application
+// that owns the device memory pool (or has reserved all of it), and real-time loops
+// that must not pay for or risk an allocation failure mid-run.  For them this entry point produces exactly what
 // eels_build_smatrix stores (S_in at every depth) in a buffer the caller passes,
 // and keeps its own work arrays in one statically sized device array that the
 // library reserves when it is loaded.  It calls no cudaMalloc/cudaFree and no
@@ -43,7 +42,9 @@ void set_err(char* err, int cap, const char* msg) {
   }
 }
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Device address of g_scratch on the current device, looked up once per device (with
+// that device current) and kept for the process; after cudaDeviceReset the kept
+// address may be stale, which the header states.
 cudaError_t scratch_ptr(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -103,7 +104,6 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
       set_err(err, err_cap, "probe aperture extends beyond the band limit");
       return EELS_ERR_ARG;
     }
-  if (n_in_out) *n_in_out = n_in;
   const int nh = n / 2;
   const int64_t plane = (int64_t)nh * nh;
   const int64_t need_out = (int64_t)n_z * n_in * plane * 8;
@@ -135,6 +135,7 @@ extern "C" eels_status eels_build_smatrix_static(const eels_specimen* spec,
     return EELS_ERR_ARG;
   }
   const int chunk = (int)std::min<size_t>((size_t)n_in, (kStaticBytes - off) / (2 * wave_bytes));
+  if (n_in_out) *n_in_out = n_in;   // written only once every check has passed
   const size_t o_w = off;
   const size_t o_phi = align256(o_w + wave_bytes * chunk);
 

@@ -17,10 +17,12 @@ from oracle import multislice as ms
 pytestmark = pytest.mark.gpu
 
 EPS_FP32 = 1e-4
-# tensor-core path: operands rounded to TF32 (unit roundoff 2^-11), FP32 accumulate
-EPS_TC = 1e-3
-# BF16 hi+lo split: each operand carries ~16 significant bits, three products
-EPS = {"fp32": EPS_FP32, "tf32": EPS_TC, "bf16x3": EPS_TC}
+# TF32 tensor cores: FP32 multislice, operands rounded to TF32, FP32 accumulate; held to
+# the FP32 bound
+EPS_TF32 = 1e-4
+# BF16 hi+lo split (three products): the reduced-precision bound
+EPS_BF16X3 = 1e-3
+EPS = {"fp32": EPS_FP32, "tf32": EPS_TF32, "bf16x3": EPS_BF16X3}
 PRECS = ("fp32", "tf32", "bf16x3")
 
 
@@ -249,6 +251,110 @@ def test_large_workloads_sampled(g, ctx, name, targets, probes):
         got = run_map(g, ctx, sm, sub, prec, assoc)
         t = np.array([got[:, iy, ix] for iy, ix in probes])
         assert eps(r, t) < EPS[prec], (prec, assoc, eps(r, t))
+
+
+@pytest.mark.parametrize("cap", [1, 3])
+def test_several_batches_per_slice_match_oracle(g, ctx, cap):
+    """Sites of one slice contracted in several batches (EELS_OPT_BATCH_SITES): the
+    batch offsets into the site, transition and tile lists are non-zero and the last
+    batch is ragged.  Element by element against the oracle in both groupings."""
+    wl = _rand(128, 2, 27, n_z=2, n_sites=14, w=12)
+    rx, ry = wl.scan_positions()
+    reached = [s for s in range(wl.n_sites)
+               if any(ms.axis_in_window(wl.site_x[s], x, wl.cell, wl.f) for x in rx)
+               and any(ms.axis_in_window(wl.site_y[s], y, wl.cell, wl.f) for y in ry)]
+    counts = np.bincount(wl.site_slice[reached], minlength=wl.n_z)
+    assert (counts > cap).all(), counts                            # every slice: > 1 batch
+    assert cap == 1 or (counts % cap != 0).any(), counts           # a ragged last batch
+    ref = lin.linear_map(wl)
+    assert ref.max() > 0
+    sm = g.build_smatrix_for(ctx, wl)
+    whole = {}
+    for prec, assoc in variants():
+        whole[(prec, assoc)] = run_map(g, ctx, sm, wl, prec, assoc)
+    ctx.set_batch_sites(cap)
+    try:
+        for prec, assoc in variants():
+            got = run_map(g, ctx, sm, wl, prec, assoc)
+            assert eps(ref, got) < EPS[prec], (prec, assoc, eps(ref, got))
+            # batching changes only the order of the FP64 sums
+            assert np.allclose(got, whole[(prec, assoc)], rtol=1e-12, atol=1e-15 * ref.max())
+    finally:
+        ctx.set_batch_sites(0)
+
+
+def test_rocksalt_small_batches_of_three_sites(g, ctx):
+    """The 128^2 rocksalt crystal (8 Fe sites per occupied slice, 3 channels) in batches
+    of three sites: 3 + 3 + 2 per slice."""
+    wl = sp.rocksalt_small()
+    ref = lin.linear_map(wl)
+    sm = g.build_smatrix_for(ctx, wl)
+    ctx.set_batch_sites(3)
+    try:
+        for prec, assoc in variants():
+            got = run_map(g, ctx, sm, wl, prec, assoc)
+            assert eps(ref, got) < EPS[prec], (prec, assoc, eps(ref, got))
+    finally:
+        ctx.set_batch_sites(0)
+
+
+# --- checkpointed S_in: segments recomputed during the backward sweep ---------------------
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_checkpointed_s_in_gives_the_same_map(g, ctx, k):
+    """A build that keeps the probe waves every k slices (EELS_OPT_SIN_CHECKPOINT) and a map
+    that recomputes S_in segment by segment: 7 slices make a short last segment.  The map
+    equals the one from the stored S_in up to the FP64 summation order, in every variant,
+    and the oracle's within tolerance."""
+    wl = _rand(128, 2, 29, n_z=7, n_sites=10, w=12)
+    ref = lin.linear_map(wl)
+    assert ref.max() > 0
+    sm = g.build_smatrix_for(ctx, wl)
+    whole = {v: run_map(g, ctx, sm, wl, *v) for v in variants()}
+    ctx.set_sin_checkpoint(k)
+    try:
+        smc = g.build_smatrix_for(ctx, wl)
+    finally:
+        ctx.set_sin_checkpoint(0)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, smc, wl, prec, assoc)
+        assert np.allclose(got, whole[(prec, assoc)], rtol=1e-12, atol=1e-15 * ref.max()), \
+            (prec, assoc)
+        assert eps(ref, got) < EPS[prec], (prec, assoc)
+    import torch
+    out = torch.empty((smc.n_in, 64, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(g.EelsError) as e:
+        smc.copy_depth(0, out)
+    assert e.value.status == 2
+    ctx.set_sout_scheme("recompute")
+    try:
+        with pytest.raises(g.EelsError) as e:
+            g.inelastic_map_for(ctx, smc, wl, "fp32")
+        assert e.value.status == 2
+    finally:
+        ctx.set_sout_scheme("stream")
+
+
+# --- failure detection: a bounded device wait that runs out ------------------------------
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers(g, ctx):
+    """EELS_OPT_WAIT_TEST withholds every TMA load of the tensor-core pipelines and cuts
+    their waits to 2e6 cycles (about a millisecond): the consumers give up with nothing in
+    flight, the kernels record it and return, and the map call reports EELS_ERR_TIMEOUT.
+    The same context then computes a correct map."""
+    wl = _rand(64, 2, 28, n_sites=4, w=8)
+    ref = ms.quadratic_map(wl)
+    sm = g.build_smatrix_for(ctx, wl)
+    for prec, assoc in (("tf32", "probe_first"), ("bf16x3", "transition_first")):
+        ctx.set_wait_test(2000)
+        try:
+            with pytest.raises(g.EelsError) as e:
+                run_map(g, ctx, sm, wl, prec, assoc)
+        finally:
+            ctx.set_wait_test(0)
+        assert e.value.status == 5 and "timed out" in str(e.value), str(e.value)
+        got = run_map(g, ctx, sm, wl, prec, assoc)
+        assert eps(ref, got) < EPS[prec], (prec, assoc)
 
 
 def test_shared_transition_potentials_equal_per_site_copies(g, ctx):
