@@ -48,7 +48,9 @@ typedef enum {
   EELS_ERR_OOM = 3,          /* device allocation failed */
   EELS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
   EELS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-  EELS_ERR_CANCELLED = 6     /* a map server request was cancelled or passed its deadline */
+  EELS_ERR_CANCELLED = 6,    /* a map server request was cancelled or passed its deadline */
+  EELS_ERR_NONFINITE = 7     /* the computed map holds NaN or Inf (non-finite inputs or an
+                                overflow); the map is still written */
 } eels_status;
 
 /* Arithmetic of the inelastic contraction (Eq. SHn0 and the |.|^2 scan sum).
@@ -149,7 +151,9 @@ eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* ds
  *   map[m][iy][ix] = f^2 sum_{sites s in window(R)} sum_d |sum_j M_{s,m}[d,j] a_j(R)|^2
  * map_out is FP64 [n_types][n_sy][n_sx], caller-owned, host or device
  * (map_on_device); it is overwritten.  beta is the EELS collection semi-angle.
- * EELS_ERR_UNSUPPORTED if the precision is not built. */
+ * The call waits for its work to finish before it returns (it reads a device status
+ * word): EELS_ERR_TIMEOUT if a bounded tensor-core wait gave up, EELS_ERR_NONFINITE if a
+ * map value is NaN or Inf.  EELS_ERR_UNSUPPORTED if the precision is not built. */
 eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
                                const eels_scan* scan, double beta, int precision,
                                double* map_out, int map_on_device, void* stream);

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libstemeels.so")
 
 EELS_PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2}
 _STATUS = {0: "EELS_OK", 1: "EELS_ERR_ARG", 2: "EELS_ERR_UNSUPPORTED", 3: "EELS_ERR_OOM",
-           4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT", 6: "EELS_ERR_CANCELLED"}
+           4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT", 6: "EELS_ERR_CANCELLED",
+           7: "EELS_ERR_NONFINITE"}
 
 
 class EelsError(RuntimeError):

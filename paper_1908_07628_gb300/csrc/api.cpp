@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 struct eels_ctx {
@@ -97,6 +99,12 @@ struct Prof {
     cudaEventCreate(&e);
     return e;
   }
+};
+
+// NVTX range over a scope (visible in nsys / ncu timelines; free when no tool attaches).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
 };
 
 // Select the context's device and drop a non-sticky error another library (or an
@@ -371,6 +379,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
                                void* stream, eels_smatrix** out) {
   if (!ctx || !out) return EELS_ERR_ARG;
   *out = nullptr;
+  Range nvtx_range("eels_build_smatrix");
   eels_status r = check_specimen(ctx, spec, op);
   if (r != EELS_OK) return r;
   EELS_CK(enter(ctx));
@@ -552,6 +561,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
                                const eels_scan* sc, double beta, int precision, double* map_out,
                                int map_on_device, void* stream) {
   if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
+  Range nvtx_range("eels_inelastic_map");
   eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
   if (r != EELS_OK) return r;
   if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32 &&
@@ -862,6 +872,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   };
   // contraction of depth i (S_out(i) in Sout) into the map
   auto contract_depth = [&](int i) -> eels_status {
+    Range nvtx_depth("contract depth");
     const float2* Sin = sm->ckpt ? seg.p + (int64_t)(i % K) * n_in * plane
                                  : sm->s_in + (int64_t)i * n_in * plane;
     if (tc && site_off[i + 1] > site_off[i]) {
@@ -943,6 +954,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   // checkpointed S-matrix: S_in(cK .. i) of the segment whose top depth is i, recomputed
   // from the checkpoint psi_j(cK) with the same row and column passes as the build
   auto recompute_segment = [&](int i) -> eels_status {
+    Range nvtx_seg("S_in segment recompute");
     const int c0 = i / K * K;
     EELS_CK(cudaMemcpyAsync(Wf.p, sm->ckpt + (int64_t)(i / K) * n_in * n * nh,
                             sizeof(float2) * (size_t)n_in * n * nh, cudaMemcpyDeviceToDevice, st));
@@ -1039,12 +1051,19 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   // coefficients carry c = f/sqrt(n_in).
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
-  EELS_CK(eels::launch_scale(dmap.p, n_map, scale, st));
-  if (tc) {
+  // device status: bit 1 a bounded tensor-core wait timed out, bit 2 the map holds NaN or
+  // Inf (the sentinel); read once the work is done
+  if (!dstatus.p) {
+    EELS_CK(dstatus.alloc(1, st));
+    EELS_CK(cudaMemsetAsync(dstatus.p, 0, sizeof(int), st));
+  }
+  EELS_CK(eels::launch_scale_check(dmap.p, n_map, scale, dstatus.p, st));
+  {
     int flag = 0;
     EELS_CK(cudaMemcpyAsync(&flag, dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     EELS_CK(cudaStreamSynchronize(st));
-    if (flag) return fail(ctx, EELS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+    if (flag & 1) return fail(ctx, EELS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+    if (flag & 2) return fail(ctx, EELS_ERR_NONFINITE, "the map holds NaN or Inf values");
   }
   if (map_on_device) {
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));

@@ -226,6 +226,18 @@ __global__ void k_scale(double* a, int64_t count, double scale) {
     a[i] *= scale;
 }
 
+// a *= scale, and bit 2 of *flag set if any scaled value is not finite (NaN or Inf)
+__global__ void k_scale_check(double* a, int64_t count, double scale, int* flag) {
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i] * scale;
+    a[i] = v;
+    bad |= !isfinite(v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 2);
+}
+
 }  // namespace
 
 cudaError_t launch_gemm1_fp32(const float2* Sout, const float2* Sin, int nh, int n_out, int n_in,
@@ -262,6 +274,13 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
 cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_accumulate<<<256, 256, 0, s>>>(acc, x, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_check(double* a, int64_t count, double scale, int* flag,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_scale_check<<<256, 256, 0, s>>>(a, count, scale, flag);
   return cudaGetLastError();
 }
 

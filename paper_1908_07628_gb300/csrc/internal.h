@@ -98,6 +98,9 @@ cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f,
                                double r0, double step, int n_pos, cudaStream_t s,
                                int transposed = 0);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
+// a *= scale; bit 2 of *flag is set if any result is NaN or Inf (the map's sentinel)
+cudaError_t launch_scale_check(double* a, int64_t count, double scale, int* flag,
+                               cudaStream_t s);
 // acc[i] += x[i]
 cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s);
 

@@ -440,12 +440,32 @@ def nanoparticle_small():
                     site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=scan)
 
 
+def nanoparticle_small_1024():
+    """The 30 A Fe-O sphere of nanoparticle_small on a 1024^2 grid (0.039 A pixels), 10
+    slices, f = 4, 48x48 scan: a few-GB case of the 1024^2 FFT plan for profiling."""
+    wl = nanoparticle_small()
+    a, box, n, f, w = A_FEO, 40.0, 1024, 4, 24
+    n_z = 10
+    x, y, z, sp = nanoparticle_atoms(a, 30.0, box)
+    lay = np.floor(z / 2.0 + 1e-9).astype(np.int32)
+    keep = lay < n_z
+    x, y, sp, lay = x[keep], y[keep], sp[keep], lay[keep]
+    vproj = projected_potentials(n, box, n_z, x, y, sp, lay)
+    fe = sp == "Fe"
+    H, wx, wy = transition_windows(n, box, w, x[fe], y[fe])
+    return Workload(name="feo_sphere30_n1024_f4", n=n, cell=box, n_z=n_z, dz=2.0,
+                    lam=wl.lam, sigma=wl.sigma, f=f, alpha=wl.alpha, beta=wl.beta, vproj=vproj,
+                    w=w, H=H, site_slice=lay[fe].astype(np.int32), site_x=x[fe].copy(),
+                    site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=wl.scan)
+
+
 WORKLOADS = {
     "rocksalt_small": rocksalt_small,
     "rocksalt_fp32": rocksalt_fp32,
     "rocksalt_vacancy": rocksalt_vacancy,
     "nanoparticle": nanoparticle,
     "nanoparticle_small": nanoparticle_small,
+    "nanoparticle_small_1024": nanoparticle_small_1024,
 }
 
 

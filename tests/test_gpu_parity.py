@@ -195,6 +195,22 @@ def test_errors_are_reported(g, ctx):
     assert e.value.status == 1
 
 
+def test_non_finite_map_is_reported(g, ctx):
+    """A NaN in one site's transition potential reaches the map: every precision returns
+    EELS_ERR_NONFINITE (the map's sentinel); finite inputs on the same context then map
+    normally."""
+    wl = _rand(64, 1, 30, n_sites=3)
+    sm = g.build_smatrix_for(ctx, wl)
+    bad = wl.with_sites(np.arange(wl.n_sites))
+    bad.H = bad.H.copy()
+    bad.H[:, 0, 2, 3] = np.nan          # every site, so that a reached one carries it
+    for prec, assoc in (("fp32", "auto"), ("tf32", "probe_first"), ("bf16x3", "transition_first")):
+        with pytest.raises(g.EelsError) as e:
+            run_map(g, ctx, sm, bad, prec, assoc)
+        assert e.value.status == 7, prec
+    assert eps(ms.quadratic_map(wl), g.inelastic_map_for(ctx, sm, wl, "fp32")) < EPS_FP32
+
+
 # --- full-size workload, sampled outputs -----------------------------------------------------
 
 def test_rocksalt_512_sampled_sites_and_probes(g, ctx):
@@ -512,10 +528,11 @@ def test_phonon_average_matches_oracle(g, ctx):
 def test_s_in_and_map_two_stage_plans(g, ctx, n, f, seed):
     """The two-stage FFT plans (512: radix 16 then 32; 768: 24 then 32; 1024: 32 then 32,
     second-stage twiddles from tables, pruned first inverse stage): S_in at every depth,
-    and the map on 512 and 768.  A cell of 0.02 A per pixel keeps the FP64 oracle's beam
-    arrays near a gigabyte."""
+    and the map on 512 and 768.  A cell of 0.012 A per pixel keeps the peak host memory of
+    the FP64 oracle near 4 GB at 768^2 (0.02 A per pixel took 10.9 GB there, enough for a
+    memory-limited test process to be killed)."""
     import torch
-    wl = _rand(n, f, seed, n_z=2, n_sites=4, w=12, cell=n * 0.02)
+    wl = _rand(n, f, seed, n_z=2, n_sites=4, w=12, cell=n * 0.012)
     s_in, beams = lin.build_s_in(wl)
     sm = g.build_smatrix_for(ctx, wl)
     nh = n // 2
