@@ -382,8 +382,10 @@ def _source_hash(kernel):
     return m.hexdigest()[:12]
 
 
-def measured_traffic(kernel, n, waves):
-    """DRAM bytes per launch from the committed ncu table, if the kernel is unchanged."""
+def measured_traffic(kernel, n, waves, operand_bytes=None):
+    """DRAM bytes per launch from the committed ncu table, if the kernel is unchanged: a
+    captured launch of the same size, or a measured ratio of DRAM bytes to operand bytes
+    applied to this launch's operand bytes."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(path).read().splitlines()
@@ -392,10 +394,29 @@ def measured_traffic(kernel, n, waves):
     for ln in lines:
         if ln.startswith("#") or not ln.strip():
             continue
-        name, nn, w, sha, nbytes = ln.split()
-        if name == kernel and int(nn) == n and w == str(waves) and sha == _source_hash(kernel):
-            return float(nbytes)
+        name, nn, w, sha, val = ln.split()
+        if name != kernel or sha != _source_hash(kernel):
+            continue
+        if w == "ratio" and operand_bytes:
+            return float(val) * operand_bytes
+        if nn != "any" and int(nn) == n and w == str(waves):
+            return float(val)
     return None
+
+
+def gemm_v_operand_bytes(wl, n_out, precision, launches):
+    """Operand bytes GEMM-V reads per launch on average: the S_out window of every site
+    and the H_t Y / -i H_t Y rows of every transition, both planes of the split."""
+    rx, ry = wl.scan_positions()
+    kal, vb = (64, 4) if precision == "bf16x3" else (32, 8)
+    k1p = (2 * wl.w * wl.w + kal - 1) // kal * kal
+    total = 0
+    for s in range(wl.n_sites):
+        nr = _window_count(wl.site_x[s], rx, wl.cell, wl.f) * \
+            _window_count(wl.site_y[s], ry, wl.cell, wl.f)
+        if nr:
+            total += (n_out + wl.n_types * 2 * nr) * k1p * vb
+    return total / max(launches, 1)
 
 
 # precision each workload's configuration names: the 1024^2 sphere and the 768^2 vacancy
@@ -585,8 +606,15 @@ def _tensor_roof(kernel, wl, n_in, n_out, prof, steps, peak, peak_src):
     avg_s = prof[kernel]["ms"] / launches / 1e3
     per_step = launches / steps
     achieved = 3 * useful / per_step / avg_s / 1e12
+    traffic = None
+    if "gemm_v" in kernel:
+        prec = "bf16x3" if "bf16x3" in kernel else "tf32"
+        traffic = measured_traffic(kernel, wl.n, "batch",
+                                   gemm_v_operand_bytes(wl, n_out, prec, per_step))
     return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "ncu DRAM bytes per operand byte of a captured batch x this launch's "
+                            "operand bytes" if traffic else None,
             "useful_tflops": useful / per_step / avg_s / 1e12,
             "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step,
             "peak_source": peak_src}
@@ -650,6 +678,19 @@ def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
     return out
 
 
+# kernels behind one profiling record: a gather record brackets three gather kernels;
+# every step also runs six small kernels outside the records (propagator table, four
+# phase tables, the final scale-and-check of the map)
+KERNELS_PER_RECORD = {"tc_gather_y": 3, "tc_gather": 3}
+UNRECORDED_PER_STEP = 6
+
+
+def kernel_launches(prof):
+    """Kernel launches of one profiled step."""
+    return sum(v["launches"] * KERNELS_PER_RECORD.get(k, 1) for k, v in prof.items()) + \
+        UNRECORDED_PER_STEP
+
+
 def _shares(prof, steps):
     tot = sum(v["ms"] for v in prof.values())
     return {k: {"launches_per_step": prof[k]["launches"] / steps,
@@ -700,7 +741,7 @@ def gpu_arm(args, rank, world, ref_samples):
     units = wl.n_scan * wl.n_z
     value = world * units / (ms_step / 1e3)
     prof, clk = res["prof"], res["clocks"]
-    launches_per_step = sum(v["launches"] for v in prof.values())
+    launches_per_step = kernel_launches(prof)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     vh = torch.from_numpy(wl.vproj).pin_memory().numpy()
@@ -727,8 +768,14 @@ def gpu_arm(args, rank, world, ref_samples):
     out = {}
     if rank == 0:
         # measured denominators: TF32 tensor (cuBLAS) and the FP32 FMA rate, this run
-        tpk = measure_peaks(g, dev)
         peaks = _peaks()
+        if args.no_peaks:   # (profiling runs) nominal figures instead of measured ones
+            tpk = {"tf32_tflops": peaks["bf16_tflops"] * 1.1 / 2.25,
+                   "tf32_tflops_sustained": peaks["bf16_tflops_sustained"] * 1.1 / 2.25,
+                   "fp32_fma_tflops": 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6,
+                   "how": "not measured (--no-peaks): bf16 x 1.1/2.25 and 152 x 128 x 2 x clock"}
+        else:
+            tpk = measure_peaks(g, dev)
         tot = {k: v["ms"] for k, v in prof.items()}
         dom = max(tot, key=tot.get) if tot else None
         out["roofline"] = _roofline(dom, wl, n_in, n_out, prof, 1, peaks, tpk, clk)
@@ -1050,6 +1097,8 @@ def main():
                     help="print the S_out scheme thickness study instead of the bench line")
     ap.add_argument("--no-elastic", action="store_true", help="skip the ADF / BF images")
     ap.add_argument("--no-extra", action="store_true", help="skip the other configurations")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the TF32 / FP32 peak measurements (nominal figures instead)")
     ap.add_argument("--phonons", type=int, default=0,
                     help="print the frozen-phonon average over this many configurations")
     ap.add_argument("--crop-study", action="store_true",
