@@ -273,10 +273,14 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  * for such a handle.  0 and 1 store every depth. */
 #define EELS_OPT_SIN_CHECKPOINT 8
 /* EELS_OPT_BATCH_SITES (>= 0, default 0): at most this many sites of one slice are
- * contracted per batch of tensor-core launches; 0 sizes the batch by a 3 GiB budget for
- * the operand buffers.  The map does not depend on it (up to FP64 summation order);
+ * contracted per batch of tensor-core launches; 0 sizes the batch by the operand budget
+ * (EELS_OPT_OPERAND_MIB).  The map does not depend on it (up to FP64 summation order);
  * smaller batches use less device memory and more launches. */
 #define EELS_OPT_BATCH_SITES 6
+/* EELS_OPT_OPERAND_MIB (>= 64, default 8192): device memory, in MiB, for the tensor-core
+ * operand buffers of one batch of sites; the batch holds as many sites of a slice as
+ * fit (at least one).  Larger batches mean fewer, longer launches. */
+#define EELS_OPT_OPERAND_MIB 9
 /* EELS_OPT_WAIT_TEST (>= 0, default 0), for failure-detection tests only: a value v > 0
  * limits every pipeline wait of the tensor-core kernels to 1000 v clock cycles and makes
  * their TMA producers issue no load, so that the consumers' bounded waits run out with

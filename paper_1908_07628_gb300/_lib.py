@@ -222,6 +222,10 @@ class Context:
         (EELS_OPT_BATCH_SITES); 0 sizes batches by the operand memory budget."""
         self._check(self._lib.eels_set_option(self._h, 6, int(cap)), "set_option")
 
+    def set_operand_budget(self, mib: int = 8192):
+        """Device memory (MiB) for one batch's tensor-core operands (EELS_OPT_OPERAND_MIB)."""
+        self._check(self._lib.eels_set_option(self._h, 9, int(mib)), "set_option")
+
     def set_sin_checkpoint(self, k: int = 0):
         """Builds keep the probe waves every k slices instead of S_in at every depth
         (EELS_OPT_SIN_CHECKPOINT); maps recompute S_in segment by segment.  0: off."""

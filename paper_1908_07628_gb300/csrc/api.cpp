@@ -26,6 +26,7 @@ struct eels_ctx {
   int sout_scheme = EELS_SOUT_STREAM;     // how S_out reaches each depth
   bool keep_exit = false;                 // builds also store S_in at the exit surface
   int sin_ckpt = 0;                       // builds checkpoint the waves every K slices (K >= 2)
+  int64_t operand_budget = (int64_t)8 << 30;   // tensor-core operand buffers of one batch
   int batch_sites = 0;                    // cap on sites per contraction batch (0: by memory)
   int wait_test = 0;                      // failure test: short pipeline waits, loads withheld
   // called between tiles of work (after each slice of a build, after each depth of a map);
@@ -276,6 +277,11 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     if (value < EELS_SOUT_STREAM || value > EELS_SOUT_INVERSE)
       return fail(ctx, EELS_ERR_ARG, "unknown S_out scheme");
     ctx->sout_scheme = value;
+    return EELS_OK;
+  }
+  if (option == EELS_OPT_OPERAND_MIB) {
+    if (value < 64) return fail(ctx, EELS_ERR_ARG, "operand budget must be >= 64 MiB");
+    ctx->operand_budget = (int64_t)value << 20;
     return EELS_OK;
   }
   if (option == EELS_OPT_SIN_CHECKPOINT) {
@@ -741,7 +747,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   int max_sites = 0;
   for (int i = 0; i < n_z; ++i) max_sites = std::max(max_sites, (int)slice_sites[i].size());
   int sb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(max_sites, 1),
-                                                       ((int64_t)3 << 30) / per_site));
+                                                       ctx->operand_budget / per_site));
   if (ctx->batch_sites > 0) sb = std::min(sb, ctx->batch_sites);
   DevBuf<float> A1, B1, M1, B2, AY, BY, BV;
   DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus, daby, dnvy, dnry;

@@ -139,6 +139,8 @@ void run_request(eels_server* sv, Request* r) {
     // the grouping follows from the request alone, never from the load (EELS_ASSOC_MODEL)
     eels_set_option(ctx, EELS_OPT_ASSOCIATION, EELS_ASSOC_MODEL);
     eels_set_option(ctx, EELS_OPT_SIN_CHECKPOINT, r->in.sin_checkpoint);
+    // operand buffers within the footprint's contraction allowance (kContractionCap)
+    eels_set_option(ctx, EELS_OPT_OPERAND_MIB, 3072);
     eels::set_tile_hook(ctx, tile_gate, r);
     bool go;
     {

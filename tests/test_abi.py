@@ -75,3 +75,40 @@ def test_workload_beam_counts():
     wl = sp.rocksalt_small()
     assert ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)[0].size == 145
     assert ms.lattice_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)[0].size == 333
+
+
+def test_request_footprint_with_s_in_checkpoints(lib):
+    """Host-only footprint model of the map server: S_in at every depth versus
+    checkpoints every K slices (probe waves as N x N/2 row spectra) plus one recomputed
+    segment and the forward work arrays during the map."""
+    import ctypes
+    import math
+    req = {"n": 1024, "n_z": 120, "cell": 68.8, "f": 2}
+    H = np.zeros((1, 2, 32, 32), np.complex64)
+    vproj = np.zeros((req["n_z"], 8, 8), np.float32)   # only the pointer and n_z are read
+    r, keep = lib.make_request(vproj, req["cell"], 0.02508, 7.29e-4, 2.15, req["f"], 0.02, H,
+                               np.zeros(1, np.int32), np.zeros(1, np.int32),
+                               np.zeros(1, np.int32), np.zeros(1), np.zeros(1),
+                               (16, 16, 0.0, 0.0, 0.1, 0.1), 0.03)
+    r.spec.n = req["n"]
+    n, nz = req["n"], req["n_z"]
+    n_in = lib.count_beams(n, req["cell"], 0.02508, req["f"], 0.02)
+    n_out = lib.count_beams(n, req["cell"], 0.02508, req["f"], 0.03)
+    c, nn, plane, wave = 8, n * n, (n // 2) ** 2 * 8, 8 * n * (n // 2)
+    h = 1 * 2 * 32 * 32 * 8
+    cap = 4 << 30
+    whole = lib.request_footprint(r)
+    expect_whole = (c * nz * nn + plane + nz * n_in * plane +
+                    max(2 * n_in * wave + 4 * nz * nn,
+                        2 * n_out * wave + n_out * plane + cap + h))
+    assert whole == expect_whole
+    k = math.ceil(math.sqrt(2 * nz))
+    r.sin_checkpoint = k
+    ck = lib.request_footprint(r)
+    expect_ck = (c * nz * nn + plane + math.ceil(nz / k) * n_in * wave +
+                 max(2 * n_in * wave + 4 * nz * nn,
+                     2 * n_out * wave + n_out * plane + cap + h + 2 * n_in * wave +
+                     k * n_in * plane))
+    assert ck == expect_ck
+    assert ck < whole / 2.5          # the largest request of the mixed stream fits in HBM
+    del keep
