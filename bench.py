@@ -742,6 +742,7 @@ def gpu_arm(args, rank, world, ref_samples):
     value = world * units / (ms_step / 1e3)
     prof, clk = res["prof"], res["clocks"]
     launches_per_step = kernel_launches(prof)
+    tuning = ctx.tuning_read()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     vh = torch.from_numpy(wl.vproj).pin_memory().numpy()
@@ -849,6 +850,7 @@ def gpu_arm(args, rank, world, ref_samples):
                   "instrumentation; kernel shares and the roofline from one more step with "
                   "events around every launch",
         "clocks": clk,
+        "autotuner": tuning,
     }
     line.update(out)
     return line

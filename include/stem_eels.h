@@ -216,9 +216,9 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
 /* Context options.
  * EELS_OPT_ASSOCIATION selects how the tensor-core contraction groups the triple
  * product sum_p conj(S_out[d,p]) H_n[p] sum_j S_in[j,p] a_j(R) (Eq. SHn0 applied to
- * the probes): EELS_ASSOC_AUTO (default) times both groupings once per contraction
- * shape on the first slice that has sites and keeps the faster one for that shape in
- * the context; EELS_ASSOC_TRANSITION_FIRST forms
+ * the probes): EELS_ASSOC_AUTO (default) times both groupings (and, with them, both
+ * tile widths of each GEMM, EELS_OPT_TILE_WIDTH) once per contraction shape on the first
+ * slice that has sites and keeps the fastest choice for that shape in the context; EELS_ASSOC_TRANSITION_FIRST forms
  * M_n = S_out^H diag(H_n) S_in and then M_n a(R) (the paper's order);
  * EELS_ASSOC_PROBE_FIRST forms Y = S_in a(R) once per site (the elastic wave inside the
  * window) and then S_out^H (H_n . Y) per channel.  Both give the same map up to rounding.
@@ -281,6 +281,13 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  * operand buffers of one batch of sites; the batch holds as many sites of a slice as
  * fit (at least one).  Larger batches mean fewer, longer launches. */
 #define EELS_OPT_OPERAND_MIB 9
+/* EELS_OPT_TILE_WIDTH (0 default, 128 or 256): columns of the output tiles of the
+ * tensor-core GEMMs (the tiles are 128 rows high).  0 lets the library choose per GEMM:
+ * EELS_ASSOC_AUTO times both widths of each GEMM together with the groupings, once per
+ * contraction shape, and keeps the faster; otherwise the narrow tile is taken where it
+ * covers the GEMM's columns with at least 5 % fewer padded columns.  The map does not
+ * depend on the width beyond rounding order. */
+#define EELS_OPT_TILE_WIDTH 10
 /* EELS_OPT_WAIT_TEST (>= 0, default 0), for failure-detection tests only: a value v > 0
  * limits every pipeline wait of the tensor-core kernels to 1000 v clock cycles and makes
  * their TMA producers issue no load, so that the consumers' bounded waits run out with
@@ -303,6 +310,13 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value);
  * lost and the call can be repeated with a larger buffer.  Disabled by default. */
 eels_status eels_profile_enable(eels_ctx* ctx, int on);
 int eels_profile_read(eels_ctx* ctx, char* buf, int cap);
+
+/* The autotuner's choices kept in the context (EELS_ASSOC_AUTO): a JSON list with one
+ * object per contraction shape {"precision", "n", "n_out", "n_in", "w", "nr_max",
+ * "n_types", "grouping", "tile_first", "tile_second"} (tile widths of the grouping's
+ * first and second GEMM).  Returns the bytes the text needs with its NUL; writes it if
+ * buf holds that many. */
+int eels_tuning_read(eels_ctx* ctx, char* buf, int cap);
 
 /* Size of the static device work array used by eels_build_smatrix_static. */
 #define EELS_STATIC_SCRATCH_BYTES (64ull << 20)

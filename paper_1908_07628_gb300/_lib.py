@@ -101,6 +101,7 @@ EXPORTS = {
                                   C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "eels_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "eels_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "eels_tuning_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "eels_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "eels_build_smatrix_static": (C.c_int, [C.POINTER(Specimen), C.POINTER(Optics), C.c_void_p,
                                             C.c_int64, C.POINTER(C.c_int), C.c_void_p,
@@ -222,6 +223,11 @@ class Context:
         (EELS_OPT_BATCH_SITES); 0 sizes batches by the operand memory budget."""
         self._check(self._lib.eels_set_option(self._h, 6, int(cap)), "set_option")
 
+    def set_tile_width(self, cols: int = 0):
+        """Output tile columns of the tensor-core GEMMs (EELS_OPT_TILE_WIDTH): 0 lets the
+        library choose (measured under the AUTO grouping), 128 or 256 forces a width."""
+        self._check(self._lib.eels_set_option(self._h, 10, int(cols)), "set_option")
+
     def set_operand_budget(self, mib: int = 8192):
         """Device memory (MiB) for one batch's tensor-core operands (EELS_OPT_OPERAND_MIB)."""
         self._check(self._lib.eels_set_option(self._h, 9, int(mib)), "set_option")
@@ -307,6 +313,14 @@ class Context:
 
     def profile_enable(self, on: bool = True):
         self._check(self._lib.eels_profile_enable(self._h, 1 if on else 0), "profile_enable")
+
+    def tuning_read(self) -> list:
+        """The autotuner's choices per contraction shape (eels_tuning_read)."""
+        import json
+        need = self._lib.eels_tuning_read(self._h, None, 0)
+        buf = C.create_string_buffer(max(need, 1))
+        self._lib.eels_tuning_read(self._h, buf, need)
+        return json.loads(buf.value.decode() or "[]")
 
     def profile_read(self) -> dict:
         """Per-kernel {launches, ms} recorded since the last read (clears the records)."""

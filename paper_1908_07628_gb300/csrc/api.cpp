@@ -27,6 +27,7 @@ struct eels_ctx {
   bool keep_exit = false;                 // builds also store S_in at the exit surface
   int sin_ckpt = 0;                       // builds checkpoint the waves every K slices (K >= 2)
   int64_t operand_budget = (int64_t)8 << 30;   // tensor-core operand buffers of one batch
+  int tile_width = 0;                     // GEMM output tile columns: 0 chosen, 128 or 256
   int batch_sites = 0;                    // cap on sites per contraction batch (0: by memory)
   int wait_test = 0;                      // failure test: short pipeline waits, loads withheld
   // called between tiles of work (after each slice of a build, after each depth of a map);
@@ -34,7 +35,10 @@ struct eels_ctx {
   eels::TileHook hook = nullptr;
   void* hook_user = nullptr;
   // measured choice of grouping per contraction shape (EELS_ASSOC_AUTO)
-  std::map<std::vector<int64_t>, int> assoc_cache;
+  // measured choice per contraction shape: grouping, and narrow (128-column) tiles for
+  // the grouping's first and second GEMM
+  struct Choice { int assoc; int narrow1, narrow2; };
+  std::map<std::vector<int64_t>, Choice> assoc_cache;
   std::string err;
   std::map<int, float2*> tw;   // device twiddle table exp(-2 pi i k/N), by N
   // kernel timing records (eels_profile_enable)
@@ -279,6 +283,12 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     ctx->sout_scheme = value;
     return EELS_OK;
   }
+  if (option == EELS_OPT_TILE_WIDTH) {
+    if (value != 0 && value != 128 && value != 256)
+      return fail(ctx, EELS_ERR_ARG, "tile width is 0, 128 or 256");
+    ctx->tile_width = value;
+    return EELS_OK;
+  }
   if (option == EELS_OPT_OPERAND_MIB) {
     if (value < 64) return fail(ctx, EELS_ERR_ARG, "operand budget must be >= 64 MiB");
     ctx->operand_budget = (int64_t)value << 20;
@@ -354,6 +364,31 @@ int eels_profile_read(eels_ctx* ctx, char* buf, int cap) {
   } else if (buf && cap > 0) {
     buf[0] = 0;
   }
+  return need;
+}
+
+int eels_tuning_read(eels_ctx* ctx, char* buf, int cap) {
+  if (!ctx) return -1;
+  std::string out = "[";
+  for (auto& kv : ctx->assoc_cache) {
+    const auto& k = kv.first;
+    const auto& c = kv.second;
+    char tmp[320];
+    std::snprintf(tmp, sizeof tmp,
+                  "%s{\"precision\": \"%s\", \"n\": %lld, \"n_out\": %lld, \"n_in\": %lld, "
+                  "\"w\": %lld, \"nr_max\": %lld, \"n_types\": %lld, \"grouping\": \"%s\", "
+                  "\"tile_first\": %d, \"tile_second\": %d}",
+                  out.size() > 1 ? ", " : "", k[0] == EELS_TC_BF16X3 ? "bf16x3" : "tf32",
+                  (long long)k[1], (long long)k[2], (long long)k[3], (long long)k[4],
+                  (long long)k[5], (long long)k[6],
+                  c.assoc == EELS_ASSOC_PROBE_FIRST ? "probe_first" : "transition_first",
+                  eels::tc_tile_width(c.narrow1), eels::tc_tile_width(c.narrow2));
+    out += tmp;
+  }
+  out += "]";
+  const int need = (int)out.size() + 1;
+  if (buf && cap >= need) std::memcpy(buf, out.c_str(), (size_t)need);
+  else if (buf && cap > 0) buf[0] = 0;
   return need;
 }
 
@@ -728,9 +763,38 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     }
     chosen = c_pr <= c_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
   }
+  // tile widths: the narrow tile when it covers the GEMM's columns with at least 5 % fewer
+  // padded columns (the rule when nothing is measured); per grouping, first and second GEMM
+  auto padded = [](int64_t cols, int64_t wd) { return (cols + wd - 1) / wd * wd; };
+  int narrow[2][2] = {};   // [grouping: 0 transition first, 1 probe first][GEMM 1st / 2nd]
+  {
+    int64_t cw = 0, cn = 0;   // second GEMM (GEMM 2 / GEMM-V): 2 n_R columns per transition
+    for (int s = 0; s < S; ++s) {
+      const int64_t nr = (int64_t)L.xcnt[s] * L.ycnt[s];
+      if (nr == 0) continue;
+      cw += T * padded(2 * nr, eels::tc_tile_width(0));
+      cn += T * padded(2 * nr, eels::tc_tile_width(1));
+    }
+    const bool n2 = cn < 0.95 * cw;
+    narrow[0][1] = narrow[1][1] = n2 ? 1 : 0;
+    auto pick = [&](int64_t cols) {
+      return padded(cols, eels::tc_tile_width(1)) < 0.95 * padded(cols, eels::tc_tile_width(0));
+    };
+    narrow[0][0] = pick(k2p) ? 1 : 0;   // GEMM 1: 2 n_in columns
+    narrow[1][0] = pick(k1p) ? 1 : 0;   // GEMM-Y: 2 w^2 columns
+    if (ctx->tile_width)                 // a width set by the caller wins
+      for (auto& row : narrow) row[0] = row[1] = ctx->tile_width == 128 ? 1 : 0;
+  }
   if (chosen == EELS_ASSOC_AUTO) {
     auto it = ctx->assoc_cache.find(shape_key);
-    if (it != ctx->assoc_cache.end()) chosen = it->second;
+    if (it != ctx->assoc_cache.end()) {
+      chosen = it->second.assoc;
+      const int gi = chosen == EELS_ASSOC_PROBE_FIRST ? 1 : 0;
+      if (!ctx->tile_width) {
+        narrow[gi][0] = it->second.narrow1;
+        narrow[gi][1] = it->second.narrow2;
+      }
+    }
   }
   bool tune = tc && chosen == EELS_ASSOC_AUTO;
   const bool need_tr = tune || chosen == EELS_ASSOC_TRANSITION_FIRST;
@@ -753,8 +817,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   DevBuf<int> dslot, dzs, dzt, dab1, dbb1, dnv1, dab2, dbb2, dnv2, dstatus, daby, dnvy, dnry;
   DevBuf<double> dscratch;
   std::vector<int> slot_all, zs_all, zt_all, nv2_all, nr_all, site_off(n_z + 1, 0);
-  std::vector<int> pv_all, py_all;
-  DevBuf<int> dtile_v, dtile_y;
+  std::vector<int> pv_all[2], py_all[2];   // [0]: 256-column tiles, [1]: 128-column tiles
+  DevBuf<int> dtile_v[2], dtile_y[2];
   if (tc) {
     for (int i = 0; i < n_z; ++i) {
       site_off[i] = (int)slot_all.size();
@@ -772,21 +836,27 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     // prefix sums of the tiles with work, over all transitions (GEMM 2 / GEMM-V: column
     // tiles of 2 n_R x every row tile of n_out) and over all sites (GEMM-Y: row tiles of
     // n_R x every column tile of 2 w^2); a batch reads its slice of them
-    const int64_t gy_v = (n_out + 127) / 128, gx_y = (k1p + 255) / 256;
-    pv_all.assign(nv2_all.size() + 1, 0);
-    for (size_t z = 0; z < nv2_all.size(); ++z)
-      pv_all[z + 1] = pv_all[z] + (int)(((int64_t)nv2_all[z] + 255) / 256 * gy_v);
-    py_all.assign(nr_all.size() + 1, 0);
-    for (size_t q = 0; q < nr_all.size(); ++q)
-      py_all[q + 1] = py_all[q] + (int)(((int64_t)nr_all[q] + 127) / 128 * gx_y);
+    // (for both tile widths: the autotuner may time both)
+    const int64_t gy_v = (n_out + 127) / 128;
+    for (int nw = 0; nw < 2; ++nw) {
+      const int64_t wd = eels::tc_tile_width(nw), gx_y = (k1p + wd - 1) / wd;
+      pv_all[nw].assign(nv2_all.size() + 1, 0);
+      for (size_t z = 0; z < nv2_all.size(); ++z)
+        pv_all[nw][z + 1] = pv_all[nw][z] + (int)(((int64_t)nv2_all[z] + wd - 1) / wd * gy_v);
+      py_all[nw].assign(nr_all.size() + 1, 0);
+      for (size_t q = 0; q < nr_all.size(); ++q)
+        py_all[nw][q + 1] = py_all[nw][q] + (int)(((int64_t)nr_all[q] + 127) / 128 * gx_y);
+    }
     std::vector<int> ab1(sb * T), bb1(sb * T), nv1(sb * T, k2p), ab2(sb * T), bb2(sb * T);
     for (int z = 0; z < sb * T; ++z) { ab1[z] = z / T; bb1[z] = z; ab2[z] = z; bb2[z] = z / T; }
     EELS_CK(dslot.upload(slot_all.data(), slot_all.size(), st));
     EELS_CK(dzs.upload(zs_all.data(), zs_all.size(), st));
     EELS_CK(dzt.upload(zt_all.data(), zt_all.size(), st));
     EELS_CK(dnv2.upload(nv2_all.data(), nv2_all.size(), st));
-    EELS_CK(dtile_v.upload(pv_all.data(), pv_all.size(), st));
-    EELS_CK(dtile_y.upload(py_all.data(), py_all.size(), st));
+    for (int nw = 0; nw < 2; ++nw) {
+      EELS_CK(dtile_v[nw].upload(pv_all[nw].data(), pv_all[nw].size(), st));
+      EELS_CK(dtile_y[nw].upload(py_all[nw].data(), py_all[nw].size(), st));
+    }
     EELS_CK(dab1.upload(ab1.data(), ab1.size(), st));
     EELS_CK(dbb1.upload(bb1.data(), bb1.size(), st));
     EELS_CK(dnv1.upload(nv1.data(), nv1.size(), st));
@@ -819,8 +889,26 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   }
   eels::WindowLists wl{dxoff.p, dxcnt.p, dxlist.p, dyoff.p, dycnt.p, dylist.p, L.max_nr};
   // tensor-core contraction of slice i with one grouping, accumulated into `map`
-  // assoc: EELS_ASSOC_TRANSITION_FIRST or EELS_ASSOC_PROBE_FIRST
-  auto contract_slice = [&](const float2* Sin, int i, int assoc, double* map) -> eels_status {
+  // assoc: EELS_ASSOC_TRANSITION_FIRST or EELS_ASSOC_PROBE_FIRST; n1, n2: narrow tiles for
+  // the first / second GEMM; timed (autotuner): event pairs around every GEMM launch,
+  // [0] first GEMM, [1] second GEMM
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[2];
+  auto timed_launch = [&](int which, bool timed, auto&& fn) -> cudaError_t {
+    cudaEvent_t a = nullptr, b2 = nullptr;
+    if (timed) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b2);
+      cudaEventRecord(a, st);
+    }
+    const cudaError_t e = fn();
+    if (timed) {
+      cudaEventRecord(b2, st);
+      tev[which].push_back({a, b2});
+    }
+    return e;
+  };
+  auto contract_slice = [&](const float2* Sin, int i, int assoc, int n1, int n2, double* map,
+                            bool timed = false) -> eels_status {
     for (int q0 = site_off[i]; q0 < site_off[i + 1]; q0 += sb) {
       const int ns = std::min(sb, site_off[i + 1] - q0);
       eels::TcBatch b{};
@@ -832,10 +920,12 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
       b.ax = ax.p; b.ay = ay.p; b.n_sx = sc->n_sx; b.n_sy = sc->n_sy;
       b.axT = axT.p; b.ayT = ayT.p;
-      b.tiles_v = dtile_v.p + (int64_t)q0 * T;
-      b.n_tiles_v = pv_all[(size_t)(q0 + ns) * T] - pv_all[(size_t)q0 * T];
-      b.tiles_y = dtile_y.p + q0;
-      b.n_tiles_y = py_all[q0 + ns] - py_all[q0];
+      b.bn_first = eels::tc_tile_width(n1);
+      b.bn_second = eels::tc_tile_width(n2);
+      b.tiles_v = dtile_v[n2].p + (int64_t)q0 * T;
+      b.n_tiles_v = pv_all[n2][(size_t)(q0 + ns) * T] - pv_all[n2][(size_t)q0 * T];
+      b.tiles_y = dtile_y[n1].p + q0;
+      b.n_tiles_y = py_all[n1][q0 + ns] - py_all[n1][q0];
       b.xoff = dxoff.p; b.xcnt = dxcnt.p; b.xlist = dxlist.p;
       b.yoff = dyoff.p; b.ycnt = dycnt.p; b.ylist = dylist.p; b.nr_cap = nr_cap;
       b.a_batch1 = dab1.p; b.b_batch1 = dbb1.p; b.n_valid1 = dnv1.p;
@@ -853,11 +943,11 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         }
         {
           Prof pr(ctx, bf ? "gemm_y_bf16x3" : "gemm_y_tf32", st);
-          EELS_CK(eels::tc_gemm_y(b, st));
+          EELS_CK(timed_launch(0, timed, [&] { return eels::tc_gemm_y(b, st); }));
         }
         {
           Prof pr(ctx, bf ? "gemm_v_abs2_bf16x3" : "gemm_v_abs2_tf32", st);
-          EELS_CK(eels::tc_gemm_v(b, st));
+          EELS_CK(timed_launch(1, timed, [&] { return eels::tc_gemm_v(b, st); }));
         }
       } else {
         {
@@ -866,11 +956,11 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
         }
         {
           Prof pr(ctx, bf ? "gemm1_bf16x3" : "gemm1_tf32", st);
-          EELS_CK(eels::tc_gemm1(b, st));
+          EELS_CK(timed_launch(0, timed, [&] { return eels::tc_gemm1(b, st); }));
         }
         {
           Prof pr(ctx, bf ? "gemm2_abs2_bf16x3" : "gemm2_abs2_tf32", st);
-          EELS_CK(eels::tc_gemm2(b, st));
+          EELS_CK(timed_launch(1, timed, [&] { return eels::tc_gemm2(b, st); }));
         }
       }
     }
@@ -882,37 +972,63 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     const float2* Sin = sm->ckpt ? seg.p + (int64_t)(i % K) * n_in * plane
                                  : sm->s_in + (int64_t)i * n_in * plane;
     if (tc && site_off[i + 1] > site_off[i]) {
+      eels_status r1 = EELS_OK;
       if (tune) {
-        // warm both groupings on the scratch map, then time each once and keep the
-        // faster; the timed transition-first run accumulates this slice into the map
-        constexpr int kGroupings = 2;
-        const int order[kGroupings] = {EELS_ASSOC_TRANSITION_FIRST, EELS_ASSOC_PROBE_FIRST};
-        EELS_CK(cudaMemsetAsync(dscratch.p, 0, sizeof(double) * n_map, st));
-        eels_status r1 = EELS_OK;
-        for (int a : order)
-          if ((r1 = contract_slice(Sin, i, a, dscratch.p)) != EELS_OK) return r1;
-        cudaEvent_t ev[kGroupings + 1];
-        for (auto& e : ev) EELS_CK(cudaEventCreate(&e));
-        EELS_CK(cudaEventRecord(ev[0], st));
-        for (int k = 0; k < kGroupings; ++k) {
-          if ((r1 = contract_slice(Sin, i, order[k], k == 0 ? dmap.p : dscratch.p)) != EELS_OK)
-            return r1;
-          EELS_CK(cudaEventRecord(ev[k + 1], st));
+        // Each grouping with both tile widths on this slice (scratch map, one warm-up run
+        // each, then one timed run with events around every GEMM launch): per grouping
+        // the faster width of each of its two GEMMs, then the grouping whose gathers and
+        // GEMMs take least.  The slice then goes once into the map with that choice.
+        const int groupings[2] = {EELS_ASSOC_TRANSITION_FIRST, EELS_ASSOC_PROBE_FIRST};
+        float best_total = -1.f;
+        int best_g = 0;
+        for (int gi = 0; gi < 2; ++gi) {
+          float tg[2][2] = {}, t_all[2] = {};   // [width][first, second GEMM]; whole slice
+          const int nw0 = ctx->tile_width ? narrow[gi][0] : 0;
+          const int nw1 = ctx->tile_width ? narrow[gi][0] : 1;
+          for (int nw = nw0; nw <= nw1; ++nw) {
+            if ((r1 = contract_slice(Sin, i, groupings[gi], nw, nw, dscratch.p)) != EELS_OK)
+              return r1;
+            cudaEvent_t e0, e1;
+            EELS_CK(cudaEventCreate(&e0));
+            EELS_CK(cudaEventCreate(&e1));
+            EELS_CK(cudaEventRecord(e0, st));
+            r1 = contract_slice(Sin, i, groupings[gi], nw, nw, dscratch.p, true);
+            EELS_CK(cudaEventRecord(e1, st));
+            EELS_CK(cudaEventSynchronize(e1));
+            cudaEventElapsedTime(&t_all[nw], e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            for (int k = 0; k < 2; ++k) {
+              for (auto& pr : tev[k]) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, pr.first, pr.second);
+                tg[nw][k] += t;
+                cudaEventDestroy(pr.first);
+                cudaEventDestroy(pr.second);
+              }
+              tev[k].clear();
+            }
+            if (r1 != EELS_OK) return r1;
+          }
+          if (!ctx->tile_width) {
+            narrow[gi][0] = tg[1][0] < tg[0][0] ? 1 : 0;
+            narrow[gi][1] = tg[1][1] < tg[0][1] ? 1 : 0;
+          }
+          const float rest = t_all[nw0] - tg[nw0][0] - tg[nw0][1];   // gathers, launch gaps
+          const float total = rest + tg[narrow[gi][0]][0] + tg[narrow[gi][1]][1];
+          if (best_total < 0.f || total < best_total) {
+            best_total = total;
+            best_g = gi;
+          }
         }
-        EELS_CK(cudaEventSynchronize(ev[kGroupings]));
-        float best = 0.f;
-        for (int k = 0; k < kGroupings; ++k) {
-          float t = 0.f;
-          cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-          if (k == 0 || t < best) { best = t; chosen = order[k]; }
-        }
-        for (auto& e : ev) cudaEventDestroy(e);
-        ctx->assoc_cache[shape_key] = chosen;
+        chosen = groupings[best_g];
+        ctx->assoc_cache[shape_key] = {chosen, narrow[best_g][0], narrow[best_g][1]};
         tune = false;
-      } else {
-        eels_status r1 = contract_slice(Sin, i, chosen, dmap.p);
-        if (r1 != EELS_OK) return r1;
       }
+      const int gi = chosen == EELS_ASSOC_PROBE_FIRST ? 1 : 0;
+      if ((r1 = contract_slice(Sin, i, chosen, narrow[gi][0], narrow[gi][1], dmap.p)) !=
+          EELS_OK)
+        return r1;
     }
     for (int b0 = slice_off[i]; !tc && b0 < slice_off[i + 1]; b0 += batch) {
       eels::TransitionBatch tb{dts.p + b0, dtt.p + b0, std::min(batch, slice_off[i + 1] - b0)};

@@ -33,7 +33,10 @@ namespace eels {
 
 namespace {
 
-constexpr int BM = 128, BN = 256;
+constexpr int BM = 128;
+// tile widths (columns of the output tile): the widest is the default, 128 suits problems
+// whose column count leaves most of a 256-wide tile empty; the autotuner picks per GEMM
+constexpr int BN_WIDE = 256, BN_NARROW = 128;
 
 template <int PREC>
 struct Prec;
@@ -43,7 +46,7 @@ struct Prec<EELS_TC_TF32> {
   static constexpr int BK = 32;         // 128 bytes of K per row
   static constexpr int PLANES = 2;      // hi, lo
   static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  static constexpr uint32_t IDESC = tc::idesc_tf32(BM, BN);
+  __host__ __device__ static constexpr uint32_t idesc(int bn) { return tc::idesc_tf32(BM, bn); }
 };
 template <>
 struct Prec<EELS_TC_BF16X3> {
@@ -51,10 +54,10 @@ struct Prec<EELS_TC_BF16X3> {
   static constexpr int BK = 64;
   static constexpr int PLANES = 2;      // hi, lo
   static constexpr CUtensorMapDataType DT = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  static constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
+  __host__ __device__ static constexpr uint32_t idesc(int bn) { return tc::idesc_bf16(BM, bn); }
 };
 
-template <int PREC>
+template <int PREC, int BN>
 struct Tile {
   using P = Prec<PREC>;
   static constexpr int A_BYTES = BM * P::BK * (int)sizeof(typename P::T);   // one plane
@@ -187,27 +190,30 @@ constexpr int THREADS = 64 + 32 * EPI_WARPS;
 // or 32 BF16 values), 64-byte swizzled, 16 KB per column half.
 constexpr int STG_ROW = 64;
 constexpr int TILE_STG = 2 * BM * STG_ROW;
-// Stages hold both planes of a 128-byte K block of A and B: 96 KB, two of them (also
-// beside the GEMM-Y staging: 2 x 96 + 2 x 16 KB).
-template <int MODE, int PREC>
+// Stages hold both planes of a 128-byte K block of A and B: 96 KB for 256-wide tiles (two
+// stages), 64 KB for 128-wide tiles (three), also beside the GEMM-Y staging (2 x 16 KB).
+template <int MODE, int PREC, int BN>
 __host__ __device__ constexpr int stages() {
-  return 2;
+  return BN == BN_WIDE ? 2 : 3;
 }
-template <int MODE, int PREC>
+template <int MODE, int PREC, int BN>
 __host__ __device__ constexpr size_t staging_half() {
   return MODE != 2 ? 0 : (size_t)TILE_STG;
 }
-template <int MODE, int PREC>
+template <int MODE, int PREC, int BN>
 __host__ __device__ constexpr size_t smem() {
-  return (size_t)stages<MODE, PREC>() * Tile<PREC>::STAGE_BYTES + 2 * staging_half<MODE, PREC>() +
-         1024 + 256;
+  return (size_t)stages<MODE, PREC, BN>() * Tile<PREC, BN>::STAGE_BYTES +
+         2 * staging_half<MODE, PREC, BN>() + 1024 + 256;
 }
-static_assert(smem<2, EELS_TC_BF16X3>() + (BN / 2) * 4 + 16 <= 232448 &&
-                  smem<2, EELS_TC_TF32>() + (BN / 2) * 4 + 16 <= 232448,
-              "GEMM-Y stages and staging exceed the shared memory of a CTA");
-static_assert(smem<1, EELS_TC_BF16X3>() + 4 * (BN / 2) * 4 + 16 <= 232448 &&
-                  smem<1, EELS_TC_TF32>() + 4 * (BN / 2) * 4 + 16 <= 232448,
-              "BF16 GEMM stages and the |.|^2 partial sums exceed the shared memory of a CTA");
+template <int PREC, int BN>
+constexpr bool fits() {
+  return smem<2, PREC, BN>() + (BN / 2) * 4 + 16 <= 232448 &&
+         smem<1, PREC, BN>() + 4 * (BN / 2) * 4 + 16 <= 232448 &&
+         smem<0, PREC, BN>() + 16 <= 232448;
+}
+static_assert(fits<EELS_TC_BF16X3, BN_WIDE>() && fits<EELS_TC_TF32, BN_WIDE>() &&
+                  fits<EELS_TC_BF16X3, BN_NARROW>() && fits<EELS_TC_TF32, BN_NARROW>(),
+              "GEMM stages, staging and partial sums exceed the shared memory of a CTA");
 }  // namespace ws
 
 // named barrier of the four epilogue warps of one column half (ids 1 and 2)
@@ -215,7 +221,7 @@ __device__ __forceinline__ void epi_sync(int half) {
   asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
 }
 
-template <int MODE, int PREC>
+template <int MODE, int PREC, int BN>
 __global__ void __launch_bounds__(ws::THREADS, 1)
 k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
              const __grid_constant__ CUtensorMap tv, int kblocks, int gx, int gy, int gz, const int* __restrict__ tile_prefix,
@@ -224,8 +230,9 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
              EpiAbs2 ea, EpiSpread ey, int* __restrict__ status, long long wait_cycles,
              int withhold) {
   using P = Prec<PREC>;
-  using TL = Tile<PREC>;
-  constexpr int S = ws::stages<MODE, PREC>(), BK = P::BK, PL = P::PLANES;
+  using TL = Tile<PREC, BN>;
+  constexpr int S = ws::stages<MODE, PREC, BN>(), BK = P::BK, PL = P::PLANES;
+  constexpr uint32_t IDESC = P::idesc(BN);
   extern __shared__ uint8_t smem_raw[];
   // |.|^2 partial sums of the column pairs, one row per TMEM lane quarter; summed in a
   // fixed order so that a map does not depend on warp scheduling
@@ -234,7 +241,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* stg = sm + S * TL::STAGE_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(stg + 2 * ws::staging_half<MODE, PREC>());
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + 2 * ws::staging_half<MODE, PREC, BN>());
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;
   uint64_t* acc_empty = acc_full + 2;
@@ -341,13 +348,13 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             const uint32_t ah = sa + kk * 32, al = sa + TL::A_BYTES + kk * 32;
             const uint32_t bh = sb + kk * 32, bl = sb + TL::B_BYTES + kk * 32;
             if constexpr (PREC == EELS_TC_TF32) {
-              tc::mma_tf32(d, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
-              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
-              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
+              tc::mma_tf32(d, tc::desc_sw128(al), tc::desc_sw128(bh), IDESC, acc);
+              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bl), IDESC, 1u);
+              tc::mma_tf32(d, tc::desc_sw128(ah), tc::desc_sw128(bh), IDESC, 1u);
             } else {
-              tc::mma_f16(d, tc::desc_sw128(al), tc::desc_sw128(bh), P::IDESC, acc);
-              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bl), P::IDESC, 1u);
-              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bh), P::IDESC, 1u);
+              tc::mma_f16(d, tc::desc_sw128(al), tc::desc_sw128(bh), IDESC, acc);
+              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bl), IDESC, 1u);
+              tc::mma_f16(d, tc::desc_sw128(ah), tc::desc_sw128(bh), IDESC, 1u);
             }
           }
           tc::mma_commit(empty + s);
@@ -365,7 +372,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
     const int half = (warp - 2) >> 2;         // column half of the tile
     const int te = threadIdx.x - 64 - 128 * half;   // 0 .. 127 within the half
     const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
-    uint8_t* stg_h = stg + (size_t)half * ws::staging_half<MODE, PREC>();
+    uint8_t* stg_h = stg + (size_t)half * ws::staging_half<MODE, PREC, BN>();
     int i = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       int z, n0, m0;
@@ -648,7 +655,8 @@ __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __r
   const int r = blockIdx.x, slot = blockIdx.y;
   const int s = slot_site[slot];
   const int nx = xcnt[s], nr = nx * ycnt[s];
-  if (2 * r >= (2 * nr + BN - 1) / BN * BN) return;   // rows of N tiles GEMM 2 skips
+  // rows of N tiles GEMM 2 skips (the widest tile: a narrower one reads no more rows)
+  if (2 * r >= (2 * nr + BN_WIDE - 1) / BN_WIDE * BN_WIDE) return;
   const int64_t pstride = (int64_t)2 * nr_cap * k2p;
   const int64_t r0 = (int64_t)slot * PL * pstride + (int64_t)(2 * r) * k2p;
   const int64_t r1 = r0 + k2p;
@@ -817,7 +825,7 @@ int sm_count() {
 
 // Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
 // kernel, except GEMM-Y in BF16 hi + lo (one CTA per tile).
-template <int MODE, int PREC>
+template <int MODE, int PREC, int BN>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tv,
                         int kblocks, int gx, int gy,
                         int gz, const int* tile_prefix, const int* a_batch, const int* b_batch,
@@ -826,19 +834,20 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
                         int valid_tiles, long long wait_cycles, int withhold) {
   if (gx <= 0 || gy <= 0 || gz <= 0) return cudaSuccess;
   static std::atomic<uint64_t> attr{0};
-  cudaError_t e = smem_attr_once(k_tc_gemm_ws<MODE, PREC>, ws::smem<MODE, PREC>(), attr);
+  cudaError_t e =
+      smem_attr_once(k_tc_gemm_ws<MODE, PREC, BN>, ws::smem<MODE, PREC, BN>(), attr);
   if (e != cudaSuccess) return e;
   const int tiles = tile_prefix ? valid_tiles : gx * gy * gz;
   if (tiles <= 0) return cudaSuccess;
   const int grid = std::min(tiles, sm_count());
   if (wait_cycles <= 0) wait_cycles = tc::kWaitCycles;   // 0: the default limit
-  k_tc_gemm_ws<MODE, PREC><<<grid, ws::THREADS, ws::smem<MODE, PREC>(), st>>>(
+  k_tc_gemm_ws<MODE, PREC, BN><<<grid, ws::THREADS, ws::smem<MODE, PREC, BN>(), st>>>(
       ta, tb, tv, kblocks, gx, gy, gz, tile_prefix, a_batch, b_batch, n_valid, m_valid, es, ea, ey,
       status, wait_cycles, withhold);
   return cudaGetLastError();
 }
 
-template <int PREC>
+template <int PREC, int BN>
 cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
   CUtensorMap mA1, mB1;
@@ -850,12 +859,12 @@ cudaError_t gemm1_impl(const TcBatch& b, cudaStream_t st) {
   EpiStore es{b.M1, Prec<PREC>::PLANES * pstride, pstride, b.k2p, b.n_out, b.k2p};
   EpiAbs2 ea{};
   EpiSpread ey{};
-  return launch_gemm<0, PREC>(mA1, mB1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
+  return launch_gemm<0, PREC, BN>(mA1, mB1, mB1, b.k1p / Prec<PREC>::BK, (b.k2p + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, nullptr, b.a_batch1,
                               b.b_batch1, b.n_valid1, nullptr, es, ea, ey, b.status, st, 0, b.wait_cycles, b.withhold);
 }
 
-template <int PREC>
+template <int PREC, int BN>
 cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
   CUtensorMap mM1, mB2;
@@ -868,7 +877,7 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  return launch_gemm<1, PREC>(mM1, mB2, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+  return launch_gemm<1, PREC, BN>(mM1, mB2, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch2, b.b_batch2, b.n_valid2, nullptr, es, ea, ey, b.status,
                               st, b.n_tiles_v, b.wait_cycles, b.withhold);
@@ -891,7 +900,7 @@ cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int PREC>
+template <int PREC, int BN>
 cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
   CUtensorMap mAY, mBY;
@@ -909,13 +918,13 @@ cudaError_t gemm_y_impl(const TcBatch& b, cudaStream_t st) {
                           ws::STG_ROW / (int)sizeof(typename Prec<PREC>::T),
                           CU_TENSOR_MAP_SWIZZLE_64B)) != cudaSuccess)
     return e;
-  return launch_gemm<2, PREC>(mAY, mBY, mBV, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
+  return launch_gemm<2, PREC, BN>(mAY, mBY, mBV, b.k2p / Prec<PREC>::BK, (b.k1p + BN - 1) / BN,
                               (b.nr_cap + BM - 1) / BM, b.n_sites, b.tiles_y, b.a_batch_y,
                               b.a_batch_y, b.n_valid_y, b.m_valid_y, es, ea, ey, b.status, st,
                               b.n_tiles_y, b.wait_cycles, b.withhold);
 }
 
-template <int PREC>
+template <int PREC, int BN>
 cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   cudaError_t e;
   CUtensorMap mA1, mBV;
@@ -927,7 +936,7 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
              b.map, b.n_out};
   EpiSpread ey{};
-  return launch_gemm<1, PREC>(mA1, mBV, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
+  return launch_gemm<1, PREC, BN>(mA1, mBV, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
                               b.a_batch1, b.b_batch1, b.n_valid2, nullptr, es, ea, ey, b.status,
                               st, b.n_tiles_v, b.wait_cycles, b.withhold);
@@ -943,14 +952,18 @@ cudaError_t tc_gather_y(const TcBatch& b, cudaStream_t st) {
 
 cudaError_t tc_gemm_y(const TcBatch& b, cudaStream_t st) {
   if (b.n_sites <= 0) return cudaSuccess;
-  return b.prec == EELS_TC_BF16X3 ? gemm_y_impl<EELS_TC_BF16X3>(b, st)
-                                  : gemm_y_impl<EELS_TC_TF32>(b, st);
+  const bool narrow = b.bn_first == BN_NARROW;
+  if (b.prec == EELS_TC_BF16X3)
+    return narrow ? gemm_y_impl<EELS_TC_BF16X3, BN_NARROW>(b, st) : gemm_y_impl<EELS_TC_BF16X3, BN_WIDE>(b, st);
+  return narrow ? gemm_y_impl<EELS_TC_TF32, BN_NARROW>(b, st) : gemm_y_impl<EELS_TC_TF32, BN_WIDE>(b, st);
 }
 
 cudaError_t tc_gemm_v(const TcBatch& b, cudaStream_t st) {
   if (b.n_sites <= 0) return cudaSuccess;
-  return b.prec == EELS_TC_BF16X3 ? gemm_v_impl<EELS_TC_BF16X3>(b, st)
-                                  : gemm_v_impl<EELS_TC_TF32>(b, st);
+  const bool narrow = b.bn_second == BN_NARROW;
+  if (b.prec == EELS_TC_BF16X3)
+    return narrow ? gemm_v_impl<EELS_TC_BF16X3, BN_NARROW>(b, st) : gemm_v_impl<EELS_TC_BF16X3, BN_WIDE>(b, st);
+  return narrow ? gemm_v_impl<EELS_TC_TF32, BN_NARROW>(b, st) : gemm_v_impl<EELS_TC_TF32, BN_WIDE>(b, st);
 }
 
 int tc_value_bytes(int prec) {
@@ -958,6 +971,8 @@ int tc_value_bytes(int prec) {
              ? Prec<EELS_TC_BF16X3>::PLANES * (int)sizeof(Prec<EELS_TC_BF16X3>::T)
              : Prec<EELS_TC_TF32>::PLANES * (int)sizeof(Prec<EELS_TC_TF32>::T);
 }
+
+int tc_tile_width(int narrow) { return narrow ? BN_NARROW : BN_WIDE; }
 
 int tc_k_align(int prec) {
   return prec == EELS_TC_BF16X3 ? Prec<EELS_TC_BF16X3>::BK : Prec<EELS_TC_TF32>::BK;
@@ -971,14 +986,18 @@ cudaError_t tc_gather(const TcBatch& b, cudaStream_t st) {
 
 cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t st) {
   if (b.n_sites <= 0) return cudaSuccess;
-  return b.prec == EELS_TC_BF16X3 ? gemm1_impl<EELS_TC_BF16X3>(b, st)
-                                  : gemm1_impl<EELS_TC_TF32>(b, st);
+  const bool narrow = b.bn_first == BN_NARROW;
+  if (b.prec == EELS_TC_BF16X3)
+    return narrow ? gemm1_impl<EELS_TC_BF16X3, BN_NARROW>(b, st) : gemm1_impl<EELS_TC_BF16X3, BN_WIDE>(b, st);
+  return narrow ? gemm1_impl<EELS_TC_TF32, BN_NARROW>(b, st) : gemm1_impl<EELS_TC_TF32, BN_WIDE>(b, st);
 }
 
 cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t st) {
   if (b.n_sites <= 0) return cudaSuccess;
-  return b.prec == EELS_TC_BF16X3 ? gemm2_impl<EELS_TC_BF16X3>(b, st)
-                                  : gemm2_impl<EELS_TC_TF32>(b, st);
+  const bool narrow = b.bn_second == BN_NARROW;
+  if (b.prec == EELS_TC_BF16X3)
+    return narrow ? gemm2_impl<EELS_TC_BF16X3, BN_NARROW>(b, st) : gemm2_impl<EELS_TC_BF16X3, BN_WIDE>(b, st);
+  return narrow ? gemm2_impl<EELS_TC_TF32, BN_NARROW>(b, st) : gemm2_impl<EELS_TC_TF32, BN_WIDE>(b, st);
 }
 
 }  // namespace eels

@@ -128,6 +128,7 @@ cudaError_t launch_cut_detect(int m, float2* X, int n_cut, const uint8_t* mask, 
 #define EELS_TC_BF16X3 1
 int tc_k_align(int prec);   // K padding (elements) of the operand buffers
 int tc_value_bytes(int prec);   // bytes per operand value, both planes
+int tc_tile_width(int narrow);   // output tile columns of the GEMMs: 128 (narrow) or 256
 struct TcBatch {
   int prec;                               // EELS_TC_TF32 or EELS_TC_BF16X3
   const float2* Sout; const float2* Sin;  // depth planes [beam][nh][nh]
@@ -161,6 +162,9 @@ struct TcBatch {
   // column tiles); n_tiles_* = the batch's total
   const int* tiles_v; int n_tiles_v;
   const int* tiles_y; int n_tiles_y;
+  // output tile width (columns, tc_tile_width) of the grouping's first GEMM (GEMM 1 /
+  // GEMM-Y) and second GEMM (GEMM 2 / GEMM-V); tiles_y and tiles_v list tiles of these widths
+  int bn_first, bn_second;
 };
 cudaError_t tc_gather(const TcBatch& b, cudaStream_t s);   // A1, B1, B2 operand buffers
 cudaError_t tc_gemm1(const TcBatch& b, cudaStream_t s);    // M1 = GEMM 1

@@ -101,6 +101,24 @@ def test_linear_map_matches_oracle(g, ctx, n, f, seed, w):
         assert eps(ref, got) < EPS[prec], (prec, assoc)
 
 
+@pytest.mark.parametrize("width", [128, 256])
+@pytest.mark.parametrize("n,f,seed,w", [(128, 3, 6, 20), (256, 2, 7, 32), (64, 2, 5, 13)])
+def test_tile_widths_match_oracle(g, ctx, width, n, f, seed, w):
+    """Both output tile widths of the tensor-core GEMMs (EELS_OPT_TILE_WIDTH), forced, in
+    every grouping and precision; column counts that are and are not multiples of 128."""
+    wl = _rand(n, f, seed, w=w, n_sites=8)
+    ref = lin.linear_map(wl) if n >= 256 else ms.quadratic_map(wl)
+    assert ref.max() > 0
+    sm = g.build_smatrix_for(ctx, wl)
+    ctx.set_tile_width(width)
+    try:
+        for prec, assoc in variants():
+            got = run_map(g, ctx, sm, wl, prec, assoc)
+            assert eps(ref, got) < EPS[prec], (width, prec, assoc, eps(ref, got))
+    finally:
+        ctx.set_tile_width(0)
+
+
 def test_rocksalt_small_full_map(g, ctx):
     wl = sp.rocksalt_small()
     ref = lin.linear_map(wl)
