@@ -174,10 +174,10 @@ struct EpiSpread {
 
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised kernel of the three GEMMs (both precisions).  Tile
-// BM x BN = 128 x 256, K blocks of 128 bytes per row.  One CTA per SM walks
+// BM x BN = 128 x 256 or 128 x 128, K blocks of 128 bytes per row.  One CTA per SM walks
 // the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 issues the TMA loads, warp 1
 // the MMAs, warps 2-9 run the epilogue (two per TMEM lane quarter, each pair splitting
-// the 256 columns).  The accumulator is double-buffered in TMEM (2 x 256 columns), so
+// the BN columns).  The accumulator is double-buffered in TMEM (2 x BN columns), so
 // the MMAs of the next tile overlap the epilogue of this one.  Every wait is bounded; a
 // failed wait stops every role (the four epilogue warps of a column half decide together
 // after their named barrier), and before returning the CTA waits, again bounded, for its
@@ -823,8 +823,8 @@ int sm_count() {
   return c;
 }
 
-// Launch of one GEMM over a (gx, gy, gz) tile grid: the persistent warp-specialised
-// kernel, except GEMM-Y in BF16 hi + lo (one CTA per tile).
+// Launch of one GEMM over a (gx, gy, gz) tile grid (or its listed tiles): the persistent
+// warp-specialised kernel, one CTA per SM at most.
 template <int MODE, int PREC, int BN>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tv,
                         int kblocks, int gx, int gy,
