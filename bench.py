@@ -1114,6 +1114,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-budget-gb", type=float, default=240.0)
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-load", type=float, default=1.5,
+                    help="offered load of the request stream, as a multiple of the service rate")
     ap.add_argument("--max-slices", type=int, default=0,
                     help="keep only the first K slices (smaller device footprint for profiling)")
     args = ap.parse_args()
@@ -1144,7 +1146,7 @@ def main():
         import paper_1908_07628_gb300 as g
         torch.cuda.init()
         res = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
-                          args.serving_slots, args.precision or "bf16x3")
+                          args.serving_slots, args.precision or "bf16x3", load=args.serving_load)
         print(json.dumps({"metric": "EELS map serving p99 latency", "value": res["p99_ms"],
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
@@ -1186,7 +1188,7 @@ def main():
         import paper_1908_07628_gb300 as g
         torch.cuda.empty_cache()
         line["serving"] = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
-                                      args.serving_slots, "bf16x3")
+                                      args.serving_slots, "bf16x3", load=args.serving_load)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
