@@ -49,8 +49,12 @@ typedef enum {
   EELS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
   EELS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
   EELS_ERR_CANCELLED = 6,    /* a map server request was cancelled or passed its deadline */
-  EELS_ERR_NONFINITE = 7     /* the computed map holds NaN or Inf (non-finite inputs or an
+  EELS_ERR_NONFINITE = 7,    /* the computed map holds NaN or Inf (non-finite inputs or an
                                 overflow); the map is still written */
+  EELS_ERR_BOUNDS = 8        /* bounds-checked debug build only (compiled with -DSTEM_CHECK):
+                                a kernel found an index it derives from a device list (window
+                                origin, beam or scan index, tile decode, TMA box coordinate)
+                                out of range and skipped that access; the result is invalid */
 } eels_status;
 
 /* Arithmetic of the inelastic contraction (Eq. SHn0 and the |.|^2 scan sum).
@@ -153,10 +157,34 @@ eels_status eels_smatrix_copy_depth(const eels_smatrix* sm, int depth, float* ds
  * (map_on_device); it is overwritten.  beta is the EELS collection semi-angle.
  * The call waits for its work to finish before it returns (it reads a device status
  * word): EELS_ERR_TIMEOUT if a bounded tensor-core wait gave up, EELS_ERR_NONFINITE if a
- * map value is NaN or Inf.  EELS_ERR_UNSUPPORTED if the precision is not built. */
+ * map value is NaN or Inf, EELS_ERR_BOUNDS (bounds-checked build only) if a kernel's
+ * index check failed.  EELS_ERR_UNSUPPORTED if the precision is not built. */
 eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
                                const eels_scan* scan, double beta, int precision,
                                double* map_out, int map_on_device, void* stream);
+
+/* The same map computed per scan tile, resumable (not in the paper: a map of a long scan
+ * can be stopped and picked up again without redoing finished positions).  The scan is
+ * cut into tiles of tile_nx x tile_ny positions (edge tiles smaller), tile k = ty * gx + tx
+ * with gx = ceil(n_sx / tile_nx), gy = ceil(n_sy / tile_ny); tile_done is caller-owned
+ * host memory of gx * gy bytes.  Tiles with tile_done[k] != 0 are skipped; every other
+ * tile is mapped, as eels_inelastic_map does over that rectangle of the scan (the stored
+ * S_in of sm is reused, the detector beams are carried backwards again per tile), its
+ * values are written into map_out (host, FP64 [n_types][n_sy][n_sx]) and tile_done[k] is
+ * set to 1.  Positions outside finished tiles are not touched.  At most max_tiles tiles
+ * are mapped per call (<= 0: no limit); *remaining (may be null) receives the number of
+ * tiles left.  On an error the tiles finished before it stay written and marked, so a
+ * later call with the same map_out and tile_done resumes there; the error codes are
+ * those of eels_inelastic_map, plus EELS_ERR_ARG for a null tile_done or a tile size
+ * below 1.  A position's value does not depend on the tiling beyond FP64 summation
+ * order when the grouping and tile width are fixed (EELS_OPT_ASSOCIATION,
+ * EELS_OPT_TILE_WIDTH); the autotuner may choose differently for differently shaped
+ * tiles (differences at the precision's rounding level). */
+eels_status eels_inelastic_map_tiles(eels_ctx* ctx, const eels_smatrix* sm,
+                                     const eels_transitions* tr, const eels_scan* scan,
+                                     double beta, int precision, int tile_nx, int tile_ny,
+                                     double* map_out, uint8_t* tile_done, int max_tiles,
+                                     int* remaining, void* stream);
 
 /* Elastic STEM images from the same S-matrix (Sec. IV D: the annular dark-field image
  * with a 60 mrad inner angle and the incoherent bright-field image whose detector has
@@ -295,6 +323,15 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
  * returns, and eels_inelastic_map returns EELS_ERR_TIMEOUT.  The context stays usable;
  * set 0 to return to normal operation. */
 #define EELS_OPT_WAIT_TEST 7
+/* EELS_OPT_CHECK_TEST (0 default, 1), for tests of the bounds-checked debug build only:
+ * eels_inelastic_map sets the window origin of the first site that some probe reaches to
+ * N/2, one past its range.
+ * Every kernel that walks a window checks the origin, records the violation and skips its
+ * work, and the call returns EELS_ERR_BOUNDS; an unchecked periodic walk from N/2 would
+ * still stay inside the plane.  The normal build returns EELS_ERR_UNSUPPORTED. */
+#define EELS_OPT_CHECK_TEST 11
+/* eels_checked_build: 1 if this library was compiled with -DSTEM_CHECK, else 0. */
+int eels_checked_build(void);
 #define EELS_OPT_SOUT_SCHEME 4
 #define EELS_SOUT_STREAM 0
 #define EELS_SOUT_RECOMPUTE 1

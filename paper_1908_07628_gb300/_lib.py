@@ -13,12 +13,15 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libstemeels.so")
+# STEM_CHECK=1: the bounds-checked debug build (build.build(check=True))
+LIB_PATH = (os.path.join(_HERE, "_build_check", "libstemeels_check.so")
+            if os.environ.get("STEM_CHECK", "") == "1"
+            else os.path.join(_HERE, "_build", "libstemeels.so"))
 
 EELS_PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2}
 _STATUS = {0: "EELS_OK", 1: "EELS_ERR_ARG", 2: "EELS_ERR_UNSUPPORTED", 3: "EELS_ERR_OOM",
            4: "EELS_ERR_CUDA", 5: "EELS_ERR_TIMEOUT", 6: "EELS_ERR_CANCELLED",
-           7: "EELS_ERR_NONFINITE"}
+           7: "EELS_ERR_NONFINITE", 8: "EELS_ERR_BOUNDS"}
 
 
 class EelsError(RuntimeError):
@@ -84,9 +87,14 @@ EXPORTS = {
     "eels_smatrix_beams": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "eels_smatrix_copy_depth": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "eels_fp32_fma_rate": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "eels_checked_build": (C.c_int, []),
     "eels_inelastic_map": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Transitions),
                                      C.POINTER(Scan), C.c_double, C.c_int, C.c_void_p, C.c_int,
                                      C.c_void_p]),
+    "eels_inelastic_map_tiles": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Transitions),
+                                           C.POINTER(Scan), C.c_double, C.c_int, C.c_int, C.c_int,
+                                           C.c_void_p, C.c_void_p, C.c_int,
+                                           C.POINTER(C.c_int), C.c_void_p]),
     "eels_quadratic_reference_map": (C.c_int, [C.c_void_p, C.POINTER(Specimen), C.POINTER(Optics),
                                                C.POINTER(Transitions), C.POINTER(Scan), C.c_double,
                                                C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -243,6 +251,11 @@ class Context:
         load, so the waits run out; 0 restores normal operation."""
         self._check(self._lib.eels_set_option(self._h, 7, int(kcycles)), "set_option")
 
+    def set_check_test(self, on: int = 1):
+        """Bounds-checked build test (EELS_OPT_CHECK_TEST): the next maps get a window
+        origin one past its range, which the checked kernels report (EELS_ERR_BOUNDS)."""
+        self._check(self._lib.eels_set_option(self._h, 11, int(on)), "set_option")
+
     def elastic_images(self, sm, scan, detectors, out=None, stream=None):
         """Elastic images [n_det][n_sy][n_sx] (FP64) for detectors [(inner, outer), ...]
         (semi-angles in rad; outer <= 0: up to the band limit)."""
@@ -363,6 +376,37 @@ class Context:
             return okeep if out is None else out
         return out
 
+    def inelastic_map_tiles(self, sm, H, site_slice, win_x0, win_y0, site_x, site_y, scan, beta,
+                            tile, map_out, tile_done, precision="fp32", max_tiles=0,
+                            stream=None):
+        """eels_inelastic_map_tiles: maps the scan tiles (tile = (tile_nx, tile_ny)) not yet
+        marked in tile_done into map_out, both numpy arrays updated in place (map_out float64
+        [n_types][n_sy][n_sx], tile_done uint8 [gy][gx]); at most max_tiles tiles (0: all).
+        Returns the number of tiles left.  On an error the finished tiles stay written and
+        marked, and the EelsError is raised."""
+        tnx, tny = int(tile[0]), int(tile[1])
+        n_sx, n_sy = int(scan[0]), int(scan[1])
+        if tnx < 1 or tny < 1:
+            raise ValueError("scan tiles need at least one position")
+        gx, gy = -(-n_sx // tnx), -(-n_sy // tny)
+        shape = (int(H.shape[-3]), n_sy, n_sx)
+        if not (isinstance(map_out, np.ndarray) and map_out.dtype == np.float64
+                and map_out.shape == shape and map_out.flags.c_contiguous):
+            raise TypeError(f"map_out must be a C-contiguous float64 numpy array {shape}")
+        if not (isinstance(tile_done, np.ndarray) and tile_done.dtype == np.uint8
+                and tile_done.size == gx * gy and tile_done.flags.c_contiguous):
+            raise TypeError(f"tile_done must be a C-contiguous uint8 numpy array of {gx * gy}")
+        tr, keep = _transitions(H, site_slice, win_x0, win_y0, site_x, site_y)
+        sc = Scan(n_sx, n_sy, *[float(v) for v in scan[2:]])
+        left = C.c_int(0)
+        st = self._lib.eels_inelastic_map_tiles(
+            self._h, sm._h, C.byref(tr), C.byref(sc), float(beta), EELS_PREC[precision], tnx,
+            tny, map_out.ctypes.data, tile_done.ctypes.data, int(max_tiles), C.byref(left),
+            _stream(stream))
+        del keep
+        self._check(st, "eels_inelastic_map_tiles")
+        return int(left.value)
+
     def quadratic_reference_map(self, vproj, cell, lam, sigma, dz, f, alpha, H, site_slice,
                                 win_x0, win_y0, site_x, site_y, scan, beta, positions=None,
                                 stream=None):
@@ -472,6 +516,11 @@ def fp32_fma_rate(device=0, iters=1 << 20) -> float:
     return out.value
 
 
+def checked_build() -> bool:
+    """True if the loaded library is the bounds-checked build (-DSTEM_CHECK)."""
+    return bool(load().eels_checked_build())
+
+
 def count_beams(n, cell, lam, f, angle) -> int:
     return int(load().eels_count_beams(int(n), float(cell), float(lam), int(f), float(angle)))
 
@@ -500,6 +549,47 @@ def inelastic_map_for(ctx: Context, sm: SMatrix, wl, precision="fp32", H=None, o
     return ctx.inelastic_map(sm, wl.H if H is None else H, wl.site_slice, wl.win_x0, wl.win_y0,
                              wl.site_x, wl.site_y, wl.scan, wl.beta, precision=precision, out=out,
                              stream=stream)
+
+
+def inelastic_map_tiles_for(ctx: Context, sm: SMatrix, wl, tile, map_out, tile_done,
+                            precision="fp32", max_tiles=0, stream=None) -> int:
+    return ctx.inelastic_map_tiles(sm, wl.H, wl.site_slice, wl.win_x0, wl.win_y0, wl.site_x,
+                                   wl.site_y, wl.scan, wl.beta, tile, map_out, tile_done,
+                                   precision=precision, max_tiles=max_tiles, stream=stream)
+
+
+def resumable_map(ctx: Context, sm: SMatrix, wl, tile, path, precision="fp32", max_tiles=0,
+                  stream=None):
+    """Map of wl per scan tile with an FP64 checkpoint file at path (.npz): the partial
+    map and the tile marks are loaded from it if it exists (it must belong to the same
+    scan, tiling, channel count and precision), and written back (to a temporary file,
+    then renamed) after every finished tile, so a process that stops between tiles loses
+    no finished tile.  At most max_tiles tiles this call (0: all).  Returns (map, tiles
+    left)."""
+    tnx, tny = int(tile[0]), int(tile[1])
+    n_sx, n_sy = int(wl.scan[0]), int(wl.scan[1])
+    gx, gy = -(-n_sx // tnx), -(-n_sy // tny)
+    key = np.array([n_sx, n_sy, tnx, tny, int(wl.H.shape[-3]), EELS_PREC[precision]],
+                   dtype=np.int64)
+    if os.path.exists(path):
+        with np.load(path) as z:
+            if not np.array_equal(z["key"], key):
+                raise ValueError(f"checkpoint {path} belongs to another map")
+            map_out = np.ascontiguousarray(z["map"], dtype=np.float64)
+            done = np.ascontiguousarray(z["done"], dtype=np.uint8)
+    else:
+        map_out = np.zeros((int(wl.H.shape[-3]), n_sy, n_sx))
+        done = np.zeros((gy, gx), dtype=np.uint8)
+    left = int((done == 0).sum())
+    mapped = 0
+    while left > 0 and (max_tiles <= 0 or mapped < max_tiles):
+        left = inelastic_map_tiles_for(ctx, sm, wl, tile, map_out, done, precision,
+                                       max_tiles=1, stream=stream)
+        mapped += 1
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, key=key, map=map_out, done=done)
+        os.replace(tmp, path)
+    return map_out, left
 
 
 def quadratic_reference_map_for(ctx: Context, wl, positions=None, stream=None):

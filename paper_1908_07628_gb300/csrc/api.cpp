@@ -30,6 +30,7 @@ struct eels_ctx {
   int tile_width = 0;                     // GEMM output tile columns: 0 chosen, 128 or 256
   int batch_sites = 0;                    // cap on sites per contraction batch (0: by memory)
   int wait_test = 0;                      // failure test: short pipeline waits, loads withheld
+  int check_test = 0;                     // bounds-checked build test: a bad window origin
   // called between tiles of work (after each slice of a build, after each depth of a map);
   // a non-zero return abandons the call with EELS_ERR_CANCELLED (the map server's gate)
   eels::TileHook hook = nullptr;
@@ -162,6 +163,36 @@ void lattice_beams(int n, double cell, double lam, int f, double angle, std::vec
         q.push_back(b);
       }
   (void)n;
+}
+
+// Bounds-checked debug build: moves every translation unit's check flag into bit 4 of
+// *status (stream-ordered after the call's kernels); nothing in the normal build.
+cudaError_t collect_checks(int* status, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = eels::collect_checks_tc(status, st)) != cudaSuccess) return e;
+  if ((e = eels::collect_checks_fp32(status, st)) != cudaSuccess) return e;
+  if ((e = eels::collect_checks_ms(status, st)) != cudaSuccess) return e;
+  return eels::collect_checks_elastic(status, st);
+}
+
+// The same for calls without a status word of their own: EELS_ERR_BOUNDS if a kernel's
+// check failed since the flags were last collected.  The flags are per process, so a
+// violation is reported by the next checked call on any context.
+eels_status bounds_verdict(eels_ctx* ctx, cudaStream_t st) {
+#ifdef STEM_CHECK
+  DevBuf<int> flag;
+  EELS_CK(flag.alloc(1, st));
+  EELS_CK(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+  EELS_CK(collect_checks(flag.p, st));
+  int h = 0;
+  EELS_CK(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  EELS_CK(cudaStreamSynchronize(st));
+  if (h & 4) return fail(ctx, EELS_ERR_BOUNDS, "a bounds check of the debug build failed");
+#else
+  (void)ctx;
+  (void)st;
+#endif
+  return EELS_OK;
 }
 
 bool inside_band(int n, int f, const std::vector<int>& p, const std::vector<int>& q) {
@@ -314,6 +345,15 @@ eels_status eels_set_option(eels_ctx* ctx, int option, int value) {
     ctx->wait_test = value;
     return EELS_OK;
   }
+  if (option == EELS_OPT_CHECK_TEST) {
+#ifdef STEM_CHECK
+    if (value != 0 && value != 1) return fail(ctx, EELS_ERR_ARG, "check test value is 0 or 1");
+    ctx->check_test = value;
+    return EELS_OK;
+#else
+    return fail(ctx, EELS_ERR_UNSUPPORTED, "needs the bounds-checked build (-DSTEM_CHECK)");
+#endif
+  }
   if (option == EELS_OPT_SHARD_COUNT) {
     if (value < 1) return fail(ctx, EELS_ERR_ARG, "shard count must be >= 1");
     ctx->shard_count = value;
@@ -390,6 +430,14 @@ int eels_tuning_read(eels_ctx* ctx, char* buf, int cap) {
   if (buf && cap >= need) std::memcpy(buf, out.c_str(), (size_t)need);
   else if (buf && cap > 0) buf[0] = 0;
   return need;
+}
+
+int eels_checked_build(void) {
+#ifdef STEM_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 int eels_count_beams(int n, double cell, double lambda, int f, double angle) {
@@ -511,6 +559,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
     e = launch_row_pass(n, n_in, W.p, nullptr, sm->t, 0, 2, sm->s_exit, n_in, plane, 0, tw, st);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "exit plane store"));
   }
+  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return bail(r);
   *out = sm;
   return EELS_OK;
 }
@@ -560,18 +609,27 @@ struct SiteLists {
   int max_nr = 0;
 };
 
-SiteLists window_lists(const eels_transitions* tr, const eels_scan* sc, double cell, int f) {
+// A rectangle of the scan: positions ix0 .. ix0 + nx - 1 by iy0 .. iy0 + ny - 1, indexed
+// from 0 within it (a scan tile; the whole scan is {0, 0, n_sx, n_sy}).
+struct ScanWin {
+  int ix0, iy0, nx, ny;
+};
+
+SiteLists window_lists(const eels_transitions* tr, const eels_scan* sc, const ScanWin& win,
+                       double cell, int f) {
   SiteLists L;
   const int S = tr->n_sites;
   L.xoff.resize(S); L.xcnt.resize(S); L.yoff.resize(S); L.ycnt.resize(S);
   for (int s = 0; s < S; ++s) {
     L.xoff[s] = (int)L.xlist.size();
-    for (int ix = 0; ix < sc->n_sx; ++ix)
-      if (axis_in_window(tr->x[s], sc->x0 + (double)ix * sc->step_x, cell, f)) L.xlist.push_back(ix);
+    for (int ix = 0; ix < win.nx; ++ix)
+      if (axis_in_window(tr->x[s], sc->x0 + (double)(win.ix0 + ix) * sc->step_x, cell, f))
+        L.xlist.push_back(ix);
     L.xcnt[s] = (int)L.xlist.size() - L.xoff[s];
     L.yoff[s] = (int)L.ylist.size();
-    for (int iy = 0; iy < sc->n_sy; ++iy)
-      if (axis_in_window(tr->y[s], sc->y0 + (double)iy * sc->step_y, cell, f)) L.ylist.push_back(iy);
+    for (int iy = 0; iy < win.ny; ++iy)
+      if (axis_in_window(tr->y[s], sc->y0 + (double)(win.iy0 + iy) * sc->step_y, cell, f))
+        L.ylist.push_back(iy);
     L.ycnt[s] = (int)L.ylist.size() - L.yoff[s];
     L.max_nr = std::max(L.max_nr, L.xcnt[s] * L.ycnt[s]);
   }
@@ -598,26 +656,24 @@ eels_status check_transitions(eels_ctx* ctx, const eels_transitions* tr, const e
 
 }  // namespace
 
-eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
-                               const eels_scan* sc, double beta, int precision, double* map_out,
-                               int map_on_device, void* stream) {
-  if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
-  Range nvtx_range("eels_inelastic_map");
-  eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
-  if (r != EELS_OK) return r;
-  if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32 &&
-      precision != EELS_PREC_BF16X3)
-    return fail(ctx, EELS_ERR_UNSUPPORTED, "precision not built");
+namespace {
+
+// The map over one rectangle of the scan, map_out [n_types][win.ny][win.nx]; the
+// arguments are checked by the callers.
+eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
+                       const eels_scan* sc, const ScanWin& win, double beta, int precision,
+                       double* map_out, int map_on_device, void* stream) {
+  eels_status r = EELS_OK;
+  bool nonfinite = false;
   const bool tc = precision != EELS_PREC_FP32;
   const int tc_prec = precision == EELS_PREC_BF16X3 ? EELS_TC_BF16X3 : EELS_TC_TF32;
-  if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
   EELS_CK(enter(ctx));
   cudaStream_t st = (cudaStream_t)stream;
   const int n = sm->n, nh = n / 2, n_z = sm->n_z, f = sm->f;
   const int n_in = (int)sm->bp.size();
   const int T = tr->n_types, w = tr->w, S = tr->n_sites;
   const int64_t plane = (int64_t)nh * nh;
-  const int64_t n_map = (int64_t)T * sc->n_sx * sc->n_sy;
+  const int64_t n_map = (int64_t)T * win.nx * win.ny;
 
   std::vector<int> dp, dq;
   lattice_beams(n, sm->cell, sm->lam, f, beta, dp, dq);
@@ -645,7 +701,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   if ((r = twiddles(ctx, n, &tw)) != EELS_OK) return r;
 
   // PRISM windows and the transitions of each slice (sites reached by some probe)
-  SiteLists L = window_lists(tr, sc, sm->cell, f);
+  SiteLists L = window_lists(tr, sc, win, sm->cell, f);
   std::vector<std::vector<int>> tr_site(n_z), tr_type(n_z);
   for (int s = 0; s < S; ++s) {
     if (L.xcnt[s] == 0 || L.ycnt[s] == 0) continue;
@@ -667,6 +723,17 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   }
   EELS_CK(dwx.upload(tr->win_x0, S, st));
   EELS_CK(dwy.upload(tr->win_y0, S, st));
+#ifdef STEM_CHECK
+  if (ctx->check_test) {   // origin N/2 for the first site some probe reaches; a periodic
+    int s0 = 0;              // walk from there still stays inside the plane
+    while (s0 < S && (L.xcnt[s0] == 0 || L.ycnt[s0] == 0)) ++s0;
+    if (s0 < S) {
+      const int bad = nh;
+      EELS_CK(cudaMemcpyAsync(dwx.p + s0, &bad, sizeof(int), cudaMemcpyHostToDevice, st));
+      EELS_CK(cudaStreamSynchronize(st));
+    }
+  }
+#endif
   EELS_CK(dxoff.upload(L.xoff.data(), S, st));
   EELS_CK(dxcnt.upload(L.xcnt.data(), S, st));
   EELS_CK(dxlist.upload(L.xlist.data(), L.xlist.size(), st));
@@ -675,18 +742,20 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   EELS_CK(dylist.upload(L.ylist.data(), L.ylist.size(), st));
   EELS_CK(dbp.upload(sm->bp.data(), n_in, st));
   EELS_CK(dbq.upload(sm->bq.data(), n_in, st));
-  EELS_CK(ax.alloc((size_t)n_in * sc->n_sx, st));
-  EELS_CK(ay.alloc((size_t)n_in * sc->n_sy, st));
-  EELS_CK(eels::launch_phase_table(ax.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x, sc->n_sx, st));
-  EELS_CK(eels::launch_phase_table(ay.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y, sc->n_sy, st));
+  EELS_CK(ax.alloc((size_t)n_in * win.nx, st));
+  EELS_CK(ay.alloc((size_t)n_in * win.ny, st));
+  EELS_CK(eels::launch_phase_table(ax.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x, win.nx, st,
+                                   0, win.ix0));
+  EELS_CK(eels::launch_phase_table(ay.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y, win.ny, st,
+                                   0, win.iy0));
   DevBuf<float2> axT, ayT;   // [pos][n_in]: the tensor-core gathers read along the beams
   if (tc) {
-    EELS_CK(axT.alloc((size_t)n_in * sc->n_sx, st));
-    EELS_CK(ayT.alloc((size_t)n_in * sc->n_sy, st));
+    EELS_CK(axT.alloc((size_t)n_in * win.nx, st));
+    EELS_CK(ayT.alloc((size_t)n_in * win.ny, st));
     EELS_CK(eels::launch_phase_table(axT.p, dbp.p, n_in, f, sm->cell, sc->x0, sc->step_x,
-                                     sc->n_sx, st, 1));
+                                     win.nx, st, 1, win.ix0));
     EELS_CK(eels::launch_phase_table(ayT.p, dbq.p, n_in, f, sm->cell, sc->y0, sc->step_y,
-                                     sc->n_sy, st, 1));
+                                     win.ny, st, 1, win.iy0));
   }
 
   // flattened transition lists of all slices
@@ -918,7 +987,7 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       b.slot_site = dslot.p + q0; b.z_site = dzs.p + (int64_t)q0 * T;
       b.z_type = dzt.p + (int64_t)q0 * T; b.n_sites = ns; b.slots_cap = sb;
       b.k1p = k1p; b.k2p = k2p; b.A1 = A1.p; b.B1 = B1.p; b.M1 = M1.p; b.B2 = B2.p;
-      b.ax = ax.p; b.ay = ay.p; b.n_sx = sc->n_sx; b.n_sy = sc->n_sy;
+      b.ax = ax.p; b.ay = ay.p; b.n_sx = win.nx; b.n_sy = win.ny;
       b.axT = axT.p; b.ayT = ayT.p;
       b.bn_first = eels::tc_tile_width(n1);
       b.bn_second = eels::tc_tile_width(n2);
@@ -1039,8 +1108,8 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
       }
       {
         Prof pr(ctx, "gemm2_abs2_fp32", st);
-        EELS_CK(eels::launch_gemm2_abs2_fp32(M.p, m_stride, n_out, n_in, ax.p, ay.p, sc->n_sx,
-                                             sc->n_sy, tb, wl, dmap.p, st));
+        EELS_CK(eels::launch_gemm2_abs2_fp32(M.p, m_stride, n_out, n_in, ax.p, ay.p, win.nx,
+                                             win.ny, tb, wl, dmap.p, st));
       }
     }
     return EELS_OK;
@@ -1174,18 +1243,21 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
   // device status: bit 1 a bounded tensor-core wait timed out, bit 2 the map holds NaN or
-  // Inf (the sentinel); read once the work is done
+  // Inf (the sentinel), bit 4 a check of the bounds-checked build failed; read once the
+  // work is done
   if (!dstatus.p) {
     EELS_CK(dstatus.alloc(1, st));
     EELS_CK(cudaMemsetAsync(dstatus.p, 0, sizeof(int), st));
   }
   EELS_CK(eels::launch_scale_check(dmap.p, n_map, scale, dstatus.p, st));
+  EELS_CK(collect_checks(dstatus.p, st));
   {
     int flag = 0;
     EELS_CK(cudaMemcpyAsync(&flag, dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     EELS_CK(cudaStreamSynchronize(st));
+    if (flag & 4) return fail(ctx, EELS_ERR_BOUNDS, "a bounds check of the debug build failed");
     if (flag & 1) return fail(ctx, EELS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
-    if (flag & 2) return fail(ctx, EELS_ERR_NONFINITE, "the map holds NaN or Inf values");
+    nonfinite = (flag & 2) != 0;
   }
   if (map_on_device) {
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
@@ -1193,6 +1265,69 @@ eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToHost, st));
     EELS_CK(cudaStreamSynchronize(st));
   }
+  if (nonfinite) return fail(ctx, EELS_ERR_NONFINITE, "the map holds NaN or Inf values");
+  return EELS_OK;
+}
+
+eels_status check_map_args(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
+                           const eels_scan* sc, double beta, int precision) {
+  eels_status r = check_transitions(ctx, tr, sc, sm->n, sm->n_z);
+  if (r != EELS_OK) return r;
+  if (precision != EELS_PREC_FP32 && precision != EELS_PREC_TF32 &&
+      precision != EELS_PREC_BF16X3)
+    return fail(ctx, EELS_ERR_UNSUPPORTED, "precision not built");
+  if (!(beta > 0)) return fail(ctx, EELS_ERR_ARG, "bad beta");
+  return EELS_OK;
+}
+
+}  // namespace
+
+eels_status eels_inelastic_map(eels_ctx* ctx, const eels_smatrix* sm, const eels_transitions* tr,
+                               const eels_scan* sc, double beta, int precision, double* map_out,
+                               int map_on_device, void* stream) {
+  if (!ctx || !sm || !map_out) return fail(ctx, EELS_ERR_ARG, "null argument");
+  Range nvtx_range("eels_inelastic_map");
+  eels_status r = check_map_args(ctx, sm, tr, sc, beta, precision);
+  if (r != EELS_OK) return r;
+  return map_window(ctx, sm, tr, sc, ScanWin{0, 0, sc->n_sx, sc->n_sy}, beta, precision, map_out,
+                    map_on_device, stream);
+}
+
+eels_status eels_inelastic_map_tiles(eels_ctx* ctx, const eels_smatrix* sm,
+                                     const eels_transitions* tr, const eels_scan* sc, double beta,
+                                     int precision, int tile_nx, int tile_ny, double* map_out,
+                                     uint8_t* tile_done, int max_tiles, int* remaining,
+                                     void* stream) {
+  if (!ctx || !sm || !map_out || !tile_done) return fail(ctx, EELS_ERR_ARG, "null argument");
+  Range nvtx_range("eels_inelastic_map_tiles");
+  eels_status r = check_map_args(ctx, sm, tr, sc, beta, precision);
+  if (r != EELS_OK) return r;
+  if (tile_nx < 1 || tile_ny < 1) return fail(ctx, EELS_ERR_ARG, "scan tiles need >= 1 position");
+  const int gx = (sc->n_sx + tile_nx - 1) / tile_nx, gy = (sc->n_sy + tile_ny - 1) / tile_ny;
+  const int T = tr->n_types;
+  int todo = 0;
+  for (int k = 0; k < gx * gy; ++k) todo += tile_done[k] ? 0 : 1;
+  if (remaining) *remaining = todo;
+  std::vector<double> part;
+  int mapped = 0;
+  for (int ty = 0; ty < gy; ++ty)
+    for (int tx = 0; tx < gx; ++tx) {
+      const int k = ty * gx + tx;
+      if (tile_done[k]) continue;
+      if (max_tiles > 0 && mapped >= max_tiles) return EELS_OK;
+      const ScanWin win{tx * tile_nx, ty * tile_ny, std::min(tile_nx, sc->n_sx - tx * tile_nx),
+                        std::min(tile_ny, sc->n_sy - ty * tile_ny)};
+      part.assign((size_t)T * win.nx * win.ny, 0.0);
+      r = map_window(ctx, sm, tr, sc, win, beta, precision, part.data(), 0, stream);
+      if (r != EELS_OK) return r;   // finished tiles stay written and marked
+      for (int m = 0; m < T; ++m)
+        for (int y = 0; y < win.ny; ++y)
+          std::memcpy(map_out + ((int64_t)m * sc->n_sy + win.iy0 + y) * sc->n_sx + win.ix0,
+                      part.data() + ((int64_t)m * win.ny + y) * win.nx, sizeof(double) * win.nx);
+      tile_done[k] = 1;
+      ++mapped;
+      if (remaining) --*remaining;
+    }
   return EELS_OK;
 }
 
@@ -1293,6 +1428,7 @@ eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eel
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
   EELS_CK(eels::launch_scale(dimg.p, n_det * n_img, scale, st));
+  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return r;
   if (out_on_device) {
     EELS_CK(cudaMemcpyAsync(out, dimg.p, sizeof(double) * n_det * n_img, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -1512,6 +1648,7 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
     k0 = k1;
   }
   if (steps) *steps = total_steps;
+  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return r;
   if (map_on_device) {
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
   } else {

@@ -478,4 +478,41 @@ __host__ __device__ constexpr bool table_twiddles_cheap() {
   return PL::NS == 2 && (PL::R(0) <= 16 || PL::per(1) > 1);
 }
 
+// ---------------------------------------------------------------------------
+// Bounds-checked debug build (-DSTEM_CHECK).  STEM_REQUIRE(c) evaluates c there: a false c
+// sets the check flag of this translation unit and the caller skips the access that c
+// guards.  In the normal build it is the constant true and c is not evaluated.  Without
+// relocatable device code every translation unit has its own flag; EELS_CHECK_COLLECTOR(fn)
+// defines fn(status, stream), which moves the unit's flag into bit 4 of a status word.
+#ifdef STEM_CHECK
+namespace {
+__device__ int g_check_flag;
+}
+__device__ __forceinline__ bool stem_require(bool ok) {
+  if (!ok) atomicOr(&g_check_flag, 1);
+  return ok;
+}
+#define STEM_REQUIRE(c) (::eels::stem_require(c))
+#define EELS_CHECK_COLLECTOR(fn)                                                 \
+  namespace {                                                                    \
+  __global__ void fn##_kernel(int* status) {                                     \
+    if (atomicExch(&g_check_flag, 0)) atomicOr(status, 4);                       \
+  }                                                                              \
+  }                                                                              \
+  cudaError_t fn(int* status, cudaStream_t s) {                                  \
+    fn##_kernel<<<1, 1, 0, s>>>(status);                                         \
+    return cudaGetLastError();                                                   \
+  }
+#else
+#define STEM_REQUIRE(c) true
+#define EELS_CHECK_COLLECTOR(fn) \
+  cudaError_t fn(int*, cudaStream_t) { return cudaSuccess; }
+#endif
+
+// A periodic window of w x w pixels with origin (x0, y0) on the nh x nh grid: the walks
+// wrap once, so the origin must lie on the grid and the window must fit in it.
+__device__ __forceinline__ bool window_ok(int x0, int y0, int w, int nh) {
+  return x0 >= 0 && x0 < nh && y0 >= 0 && y0 < nh && w >= 1 && w <= nh;
+}
+
 }  // namespace eels

@@ -39,6 +39,9 @@ k_gemm1(const float2* __restrict__ Sout, const float2* __restrict__ Sin, int nh,
   __shared__ float2 hk[TK];
   const int t = blockIdx.z;
   const int s = tr_site[t];
+  if (!STEM_REQUIRE(s >= 0 && tr_type[t] >= 0 && tr_type[t] < n_types &&
+                    window_ok(win_x0[s], win_y0[s], w, nh)))
+    return;   // the whole block, before any barrier
   const float2* Ht = H + ((int64_t)s * h_mul * n_types + tr_type[t]) * w * w;
   const int x0 = win_x0[s], y0 = win_y0[s];
   const int d0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
@@ -135,6 +138,9 @@ k_gemm2_abs2(const float2* __restrict__ M, int64_t m_stride, int n_out, int n_in
     if (r < nr) {
       rix[threadIdx.x] = xlist[xoff[s] + r % nx];
       riy[threadIdx.x] = ylist[yoff[s] + r / nx];
+      if (!STEM_REQUIRE(rix[threadIdx.x] >= 0 && rix[threadIdx.x] < n_sx &&
+                        riy[threadIdx.x] >= 0 && riy[threadIdx.x] < n_sy && tr_type[t] >= 0))
+        rix[threadIdx.x] = riy[threadIdx.x] = -1;   // skipped below
     } else {
       rix[threadIdx.x] = -1;
       riy[threadIdx.x] = -1;
@@ -199,12 +205,12 @@ k_gemm2_abs2(const float2* __restrict__ M, int64_t m_stride, int n_out, int n_in
 
 __global__ void k_phase_table(float2* __restrict__ out, const int* __restrict__ bidx, int n_beams,
                               int f, double cell, double r0, double step, int n_pos,
-                              int transposed) {
+                              int transposed, int r_first) {
   const int total = n_beams * n_pos;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int j = transposed ? i % n_beams : i / n_pos;
     const int r = transposed ? i / n_beams : i % n_pos;
-    const double R = __dadd_rn(r0, __dmul_rn((double)r, step));
+    const double R = __dadd_rn(r0, __dmul_rn((double)(r_first + r), step));
     double cyc = (double)f * (double)bidx[j] * R / cell;   // exp(-2 pi i cyc)
     cyc -= floor(cyc);
     double s, c;
@@ -263,11 +269,12 @@ cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out,
 }
 
 cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
-                               double r0, double step, int n_pos, cudaStream_t s, int transposed) {
+                               double r0, double step, int n_pos, cudaStream_t s, int transposed,
+                               int r_first) {
   const int total = n_beams * n_pos;
   if (total <= 0) return cudaSuccess;
   k_phase_table<<<(total + 255) / 256, 256, 0, s>>>(out, bidx, n_beams, f, cell, r0, step, n_pos,
-                                                    transposed);
+                                                    transposed, r_first);
   return cudaGetLastError();
 }
 
@@ -289,5 +296,7 @@ cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s)
   k_scale<<<256, 256, 0, s>>>(a, count, scale);
   return cudaGetLastError();
 }
+
+EELS_CHECK_COLLECTOR(collect_checks_fp32)
 
 }  // namespace eels

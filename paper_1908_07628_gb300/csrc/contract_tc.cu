@@ -154,6 +154,7 @@ struct EpiAbs2 {
   int n_sx, n_sy;
   double* map;
   int rows;
+  int n_types;           // map planes (checked in the bounds-checked build)
 };
 
 // GEMM-Y epilogue: C[r][2p + c] = Y[r][p] of one site; for every channel t write
@@ -292,6 +293,10 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
       z = lo;
       const int local = t - (tile_prefix[z] - base);
       const int count = tile_prefix[z + 1] - tile_prefix[z];
+      // a problem's tiles form a rectangle of whole rows of the tile grid
+      if (!STEM_REQUIRE(count > 0 && count % (MODE == 2 ? gx : gy) == 0 && count <= gx * gy &&
+                        local >= 0 && local < count))
+        return false;
       const int nx = MODE == 2 ? gx : count / gy;
       n0 = (local % nx) * BN;
       m0 = (local / nx) * BM;
@@ -308,6 +313,7 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
         int z, n0, m0;
         if (!decode(t, z, n0, m0)) continue;
         const int ab = a_batch[z], bb = b_batch[z];
+        (void)STEM_REQUIRE(ab >= 0 && bb >= 0);   // TMA box coordinates of the problem
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const int s = it % S;
           if (it >= S && !(ok = tc::mbar_wait(empty + s, ((it / S) - 1) & 1, wait_cycles))) break;
@@ -405,6 +411,13 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
         constexpr int CC = ws::STG_ROW / (int)sizeof(typename P::T);   // 16 TF32, 32 BF16
         constexpr int PX = CC / 2;
         const int site = ey.slot_site[z];
+        if (!STEM_REQUIRE(site >= 0)) {   // skip the tile, keeping the TMEM handshake below
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(acc_empty + b);
+          ++i;
+          continue;
+        }
         const int rr = 2 * (q4 * 32 + lane);
         for (int c = c_lo; c < c_hi && n0 + c < es.cols; c += CC) {
           for (int t0 = 0; t0 < ey.n_types; ++t0) {
@@ -454,7 +467,9 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
               }
               tc::fence_async_shared();
               epi_sync(half);
-              if (te == 0) {
+              // a store box starts at non-negative coordinates, x on a 16-byte boundary
+              if (te == 0 && STEM_REQUIRE(n0 + c >= 0 && ((n0 + c) * (int)sizeof(typename P::T)) % 16 == 0 &&
+                                          m0 >= 0 && z * ey.n_types + t0 >= 0)) {
                 tc::tma_store_4d(&tv, stg_h, n0 + c, 2 * m0, pl, z * ey.n_types + t0);
                 tc::bulk_commit();
               }
@@ -495,10 +510,14 @@ k_tc_gemm_ws(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
         const int nv = n_valid[z];
         for (int k = c_lo / 2 + te; k < c_hi / 2; k += 128) {
           const int r = n0 / 2 + k;
-          if (2 * r < nv) {
+          if (2 * r < nv && STEM_REQUIRE(s >= 0 && nx > 0)) {
             const int ix = ea.xlist[ea.xoff[s] + r % nx];
             const int iy = ea.ylist[ea.yoff[s] + r / nx];
-            const int64_t idx = ((int64_t)ea.z_type[z] * ea.n_sy + iy) * ea.n_sx + ix;
+            const int ty = ea.z_type[z];
+            if (!STEM_REQUIRE(ix >= 0 && ix < ea.n_sx && iy >= 0 && iy < ea.n_sy && ty >= 0 &&
+                              ty < ea.n_types))
+              continue;
+            const int64_t idx = ((int64_t)ty * ea.n_sy + iy) * ea.n_sx + ix;
             atomicAdd(ea.map + idx, (double)(((red[0][k] + red[1][k]) + red[2][k]) + red[3][k]));
           }
         }
@@ -576,6 +595,7 @@ __global__ void k_gather_sout(const float2* __restrict__ Sout, int nh, int n_out
   constexpr int PL = Prec<PREC>::PLANES;
   const int d0 = blockIdx.x * kSoutBeams, slot = blockIdx.y;
   const int s = slot_site[slot];
+  if (!STEM_REQUIRE(s >= 0 && window_ok(wx[s], wy[s], w, nh))) return;   // whole block
   const int64_t plane = (int64_t)nh * nh;
   const int64_t pstride = (int64_t)n_out * k1p;
   const int64_t rbase = (int64_t)slot * PL * pstride + (int64_t)d0 * k1p;
@@ -615,6 +635,9 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
   constexpr int PL = Prec<PREC>::PLANES;
   const int j = blockIdx.x, z = blockIdx.y;
   const int s = z_site[z];
+  if (!STEM_REQUIRE(s >= 0 && z_type[z] >= 0 && z_type[z] < n_types &&
+                    window_ok(wx[s], wy[s], w, nh)))
+    return;   // the whole block
   const int64_t plane = (int64_t)nh * nh;
   const int64_t pstride = (int64_t)2 * n_in * k1p;
   const int64_t r0 = (int64_t)z * PL * pstride + (int64_t)(2 * j) * k1p;
@@ -646,7 +669,7 @@ __global__ void k_gather_sin_h(const float2* __restrict__ Sin, int nh, int n_in,
 // a_r[j] = ax[j][ix(r)] ay[j][iy(r)]
 template <int PREC>
 __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __restrict__ ayT,
-                               int n_in, const int* __restrict__ slot_site,
+                               int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
                                const int* __restrict__ xoff, const int* __restrict__ xcnt,
                                const int* __restrict__ xlist, const int* __restrict__ yoff,
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
@@ -664,6 +687,7 @@ __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __r
   if (r < nr) {
     ix = xlist[xoff[s] + r % nx];
     iy = ylist[yoff[s] + r / nx];
+    if (!STEM_REQUIRE(ix >= 0 && ix < n_sx && iy >= 0 && iy < n_sy)) ix = iy = 0;
   }
   const float2* axr = axT + (int64_t)ix * n_in;
   const float2* ayr = ayT + (int64_t)iy * n_in;
@@ -680,7 +704,7 @@ __global__ void k_gather_probe(const float2* __restrict__ axT, const float2* __r
 // by the first kArowRows threads) and writes them four at a time.
 template <int PREC>
 __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __restrict__ ayT,
-                               int n_in, const int* __restrict__ slot_site,
+                               int n_in, int n_sx, int n_sy, const int* __restrict__ slot_site,
                                const int* __restrict__ xoff, const int* __restrict__ xcnt,
                                const int* __restrict__ xlist, const int* __restrict__ yoff,
                                const int* __restrict__ ycnt, const int* __restrict__ ylist,
@@ -696,6 +720,9 @@ __global__ void k_gather_arows(const float2* __restrict__ axT, const float2* __r
     const int r = rb + threadIdx.x;
     s_ix[threadIdx.x] = r < nr ? xlist[xoff[s] + r % nx] : -1;   // -1: a zero row
     s_iy[threadIdx.x] = r < nr ? ylist[yoff[s] + r / nx] : -1;
+    if (r < nr && !STEM_REQUIRE(s_ix[threadIdx.x] >= 0 && s_ix[threadIdx.x] < n_sx &&
+                                s_iy[threadIdx.x] >= 0 && s_iy[threadIdx.x] < n_sy))
+      s_ix[threadIdx.x] = s_iy[threadIdx.x] = -1;
   }
   __syncthreads();
   const int rows = min(kArowRows, r_end - rb);
@@ -731,6 +758,7 @@ __global__ void k_gather_sin_t(const float2* __restrict__ Sin, int nh, int n_in,
   __shared__ float2 tile[32][33];
   const int p0 = blockIdx.x * 32, j0 = blockIdx.y * 32, slot = blockIdx.z;
   const int s = slot_site[slot];
+  if (!STEM_REQUIRE(s >= 0 && window_ok(wx[s], wy[s], w, nh))) return;   // before any barrier
   const int P = w * w;
   const int64_t plane = (int64_t)nh * nh;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
@@ -805,7 +833,7 @@ cudaError_t gather_impl(const TcBatch& b, cudaStream_t st) {
                                                           b.wy, b.B1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_probe<PREC><<<dim3(b.nr_cap, b.n_sites), 256, 0, st>>>(
-      b.axT, b.ayT, b.n_in, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
+      b.axT, b.ayT, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
       b.nr_cap, b.B2, b.k2p);
   return cudaGetLastError();
 }
@@ -875,7 +903,7 @@ cudaError_t gemm2_impl(const TcBatch& b, cudaStream_t st) {
     return e;
   EpiStore es{};
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
-             b.map, b.n_out};
+             b.map, b.n_out, b.n_types};
   EpiSpread ey{};
   return launch_gemm<1, PREC, BN>(mM1, mB2, mB2, b.k2p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
@@ -891,7 +919,7 @@ cudaError_t gather_y_impl(const TcBatch& b, cudaStream_t st) {
       b.Sout, b.nh, b.n_out, b.w, b.slot_site, b.wx, b.wy, b.A1, b.k1p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_arows<PREC><<<dim3((b.nr_cap + kArowRows - 1) / kArowRows, b.n_sites), 256, 0, st>>>(
-      b.axT, b.ayT, b.n_in, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
+      b.axT, b.ayT, b.n_in, b.n_sx, b.n_sy, b.slot_site, b.xoff, b.xcnt, b.xlist, b.yoff, b.ycnt, b.ylist,
       b.nr_cap, b.AY, b.k2p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   dim3 gt((b.k1p / 2 + 31) / 32, (b.k2p / 2 + 31) / 32, b.n_sites);
@@ -934,7 +962,7 @@ cudaError_t gemm_v_impl(const TcBatch& b, cudaStream_t st) {
     return e;
   EpiStore es{};
   EpiAbs2 ea{b.z_site, b.z_type, b.xoff, b.xcnt, b.xlist, b.yoff, b.ylist, b.n_sx, b.n_sy,
-             b.map, b.n_out};
+             b.map, b.n_out, b.n_types};
   EpiSpread ey{};
   return launch_gemm<1, PREC, BN>(mA1, mBV, mBV, b.k1p / Prec<PREC>::BK, (2 * b.nr_cap + BN - 1) / BN,
                               (b.n_out + BM - 1) / BM, b.n_sites * b.n_types, b.tiles_v,
@@ -999,5 +1027,7 @@ cudaError_t tc_gemm2(const TcBatch& b, cudaStream_t st) {
     return narrow ? gemm2_impl<EELS_TC_BF16X3, BN_NARROW>(b, st) : gemm2_impl<EELS_TC_BF16X3, BN_WIDE>(b, st);
   return narrow ? gemm2_impl<EELS_TC_TF32, BN_NARROW>(b, st) : gemm2_impl<EELS_TC_TF32, BN_WIDE>(b, st);
 }
+
+EELS_CHECK_COLLECTOR(collect_checks_tc)
 
 }  // namespace eels

@@ -39,10 +39,16 @@ k_exit_cut(const float2* __restrict__ S, int n_in, int nh, int m,
   const int yp = blockIdx.y;
   const int iyl = blockIdx.z;
   const int iy = iy0 + iyl;
+  // window origins on the grid (the block's row origin and first column origin decide
+  // for the whole block; a bad later column origin is replaced by the first)
+  if (!STEM_REQUIRE(wy[iy] >= 0 && wy[iy] < nh && wx[ix0] >= 0 && wx[ix0] < nh)) return;
   const int y = (wy[iy] + yp) % nh;
   const int xa = wx[ix0];
-  if (threadIdx.x < kCutProbes)
-    dx[threadIdx.x] = threadIdx.x < np ? (wx[ix0 + threadIdx.x] - xa + nh) % nh : 0;
+  if (threadIdx.x < kCutProbes) {
+    int xg = threadIdx.x < np ? wx[ix0 + threadIdx.x] : xa;
+    if (!STEM_REQUIRE(xg >= 0 && xg < nh)) xg = xa;
+    dx[threadIdx.x] = (xg - xa + nh) % nh;
+  }
   __syncthreads();
   int span = 0;
   for (int g = 0; g < np; ++g) span = max(span, dx[g]);
@@ -274,5 +280,7 @@ cudaError_t launch_cut_detect(int m, float2* X, int n_cut, const uint8_t* mask, 
       return cudaErrorInvalidValue;
   }
 }
+
+EELS_CHECK_COLLECTOR(collect_checks_elastic)
 
 }  // namespace eels

@@ -92,15 +92,22 @@ cudaError_t launch_gemm2_abs2_fp32(const float2* M, int64_t m_stride, int n_out,
                                    const float2* ax, const float2* ay, int n_sx, int n_sy,
                                    const TransitionBatch& tb, const WindowLists& wl, double* map,
                                    cudaStream_t s);
-// ax[j][ix] = exp(-2 pi i f p_j Rx(ix) / L) (FP64 phase); same for ay with q_j, Ry.
+// ax[j][ix] = exp(-2 pi i f p_j Rx(ix) / L) (FP64 phase); same for ay with q_j, Ry.  Row
+// ix holds position Rx = r0 + (r_first + ix) step (a window of a longer scan line).
 // transposed = 1 writes out[pos][j] instead (coalesced reads along the beams).
 cudaError_t launch_phase_table(float2* out, const int* bidx, int n_beams, int f, double cell,
                                double r0, double step, int n_pos, cudaStream_t s,
-                               int transposed = 0);
+                               int transposed = 0, int r_first = 0);
 cudaError_t launch_scale(double* a, int64_t count, double scale, cudaStream_t s);
 // a *= scale; bit 2 of *flag is set if any result is NaN or Inf (the map's sentinel)
 cudaError_t launch_scale_check(double* a, int64_t count, double scale, int* flag,
                                cudaStream_t s);
+// Bounds-checked debug build: each collector moves its translation unit's check flag into
+// bit 4 of *status (and clears it); in the normal build they do nothing.
+cudaError_t collect_checks_tc(int* status, cudaStream_t s);        // contract_tc.cu
+cudaError_t collect_checks_fp32(int* status, cudaStream_t s);      // contract_fp32.cu
+cudaError_t collect_checks_ms(int* status, cudaStream_t s);        // multislice.cu
+cudaError_t collect_checks_elastic(int* status, cudaStream_t s);   // elastic.cu
 // acc[i] += x[i]
 cudaError_t launch_accumulate(double* acc, const double* x, int64_t count, cudaStream_t s);
 

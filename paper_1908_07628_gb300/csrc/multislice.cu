@@ -314,6 +314,7 @@ __global__ void k_init_plane_waves(float2* __restrict__ W, int n, const int* __r
                                    const float2* __restrict__ tw) {
   const int nh = n / 2, npair = nh / 2;
   const int64_t wave = blockIdx.y;
+  if (!STEM_REQUIRE(px[wave] >= -nh && px[wave] < nh)) return;   // beam column on the grid
   const int col = px[wave] >= 0 ? px[wave] : px[wave] + nh;
   const float2 a = amp[wave];
   const int q = py[wave];
@@ -391,6 +392,9 @@ __global__ void k_spawn(int n, const int* __restrict__ src, const int* __restric
   const int y = blockIdx.x;
   const int k = blockIdx.y;
   const int s = site[k];
+  if (!STEM_REQUIRE(s >= 0 && src[k] >= 0 && type[k] >= 0 && type[k] < n_types &&
+                    window_ok(win_x0[s], win_y0[s], w, nh)))
+    return;   // the whole block, before any barrier
   const int64_t wave = first_wave + k;
   float2* dst = Phi + (wave * n + y) * nh;
   int v = -1;
@@ -550,5 +554,7 @@ cudaError_t launch_spawn(int n, const SpawnList& sp, const float2* D, const floa
                                   h_mul, w, win_x0, win_y0, Phi, tw);
   return cudaGetLastError();
 }
+
+EELS_CHECK_COLLECTOR(collect_checks_ms)
 
 }  // namespace eels
