@@ -971,7 +971,7 @@ def _predicted_service_s(req, g):
     return ms_s + 8 * min(tr, pr) / 600e12
 
 
-def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4):
+def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4, log_path=None):
     """Seeded Poisson stream of mixed map requests through the map server."""
     redrawn = []
 
@@ -1023,6 +1023,12 @@ def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4):
         except g.EelsError as e:
             errors.append(str(e)[:120])
     st = srv.stats()
+    infos = [srv.info(i) for i in ids]
+    if log_path:   # one JSON line per request
+        srv.log_jsonl(log_path, ids, extra={i: {"n": req["n"], "n_z": req["n_z"],
+                                                "n_types": req["n_types"], "f": req["f"],
+                                                "precision": precision}
+                                            for i, req in zip(ids, stream)})
     srv.close()
     fps = [footprint(req) for req in stream]
     return {"requests": n_requests, "slots": slots, "hbm_budget_gb": budget / 2 ** 30,
@@ -1035,6 +1041,8 @@ def serving_run(g, n_requests, budget, slots, precision, load=1.5, seed=4):
             "mean_wait_ms": st["mean_wait_ms"], "makespan_s": st["makespan_s"],
             "pixel_slices_per_s": st["pixel_slices_per_s"], "completed": st["completed"],
             "failed": st["failed"], "peak_gb": st["peak_bytes"] / 2 ** 30,
+            "wave_steps": sum(d["wave_steps"] for d in infos if d["status"] == 0),
+            "contraction_tflop": sum(d["contraction_flops"] for d in infos) / 1e12,
             "redrawn_over_budget": len(redrawn), "redrawn_shapes": redrawn[:16],
             "stream": "seeded (4) mixed rocksalt requests: grids 256^2-1024^2, 20-120 slices, "
                       "1-6 channels, f 2-4, scans 16^2-64^2; Poisson arrivals at the offered "
@@ -1114,6 +1122,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-budget-gb", type=float, default=240.0)
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-log", default=None,
+                    help="append one JSON line per serving request to this file")
     ap.add_argument("--serving-load", type=float, default=1.5,
                     help="offered load of the request stream, as a multiple of the service rate")
     ap.add_argument("--max-slices", type=int, default=0,
@@ -1146,7 +1156,8 @@ def main():
         import paper_1908_07628_gb300 as g
         torch.cuda.init()
         res = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
-                          args.serving_slots, args.precision or "bf16x3", load=args.serving_load)
+                          args.serving_slots, args.precision or "bf16x3", load=args.serving_load,
+                          log_path=args.serving_log)
         print(json.dumps({"metric": "EELS map serving p99 latency", "value": res["p99_ms"],
                           "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                           "data": "synthetic", "serving": res,
@@ -1188,7 +1199,8 @@ def main():
         import paper_1908_07628_gb300 as g
         torch.cuda.empty_cache()
         line["serving"] = serving_run(g, args.serving_requests, int(args.serving_budget_gb * 2 ** 30),
-                                      args.serving_slots, "bf16x3", load=args.serving_load)
+                                      args.serving_slots, "bf16x3", load=args.serving_load,
+                                      log_path=args.serving_log)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

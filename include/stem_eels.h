@@ -437,6 +437,13 @@ typedef struct {
   double t_submit, t_admit, t_first_tile, t_done;
   int tiles;                /* tiles issued */
   int64_t footprint;        /* device bytes reserved while admitted */
+  int n_in, n_out;          /* probe beams (alpha) and detector beams (beta) on the f-lattice */
+  int64_t pixel_slices;     /* n_sx n_sy n_z */
+  int64_t wave_steps;       /* multislice wave-slice steps issued for the request: n_in n_z
+                               (build) + n_out n_z (S_out stream) + n_in n_z again when S_in
+                               is checkpointed (segment recompute) */
+  double contraction_flops; /* flops of the map's contraction as grouped, 8 per complex
+                               product (once finished; 0 before) */
 } eels_request_info;
 
 /* Device bytes the server reserves for a request while it runs: transmissions, S_in (or

@@ -61,7 +61,9 @@ class Request(C.Structure):
 class RequestInfo(C.Structure):
     _fields_ = [("done", C.c_int), ("status", C.c_int), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_first_tile", C.c_double), ("t_done", C.c_double),
-                ("tiles", C.c_int), ("footprint", C.c_int64)]
+                ("tiles", C.c_int), ("footprint", C.c_int64), ("n_in", C.c_int),
+                ("n_out", C.c_int), ("pixel_slices", C.c_int64), ("wave_steps", C.c_int64),
+                ("contraction_flops", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -669,6 +671,25 @@ class Server:
         if st != 0:
             raise EelsError(st, "eels_server_request_info")
         return {name: getattr(r, name) for name, _ in RequestInfo._fields_}
+
+    def log_jsonl(self, path, rids, extra=None):
+        """Appends one JSON line per request (eels_server_request_info plus the derived
+        latency, wait and pixel-slices/s) to path; extra (a dict per request id) is merged
+        into its line."""
+        import json
+        with open(path, "a") as fh:
+            for rid in rids:
+                d = self.info(rid)
+                d["id"] = int(rid)
+                done, first, sub = d["t_done"], d["t_first_tile"], d["t_submit"]
+                d["latency_s"] = done - sub if d["done"] and done >= 0 else None
+                d["wait_s"] = first - sub if first >= 0 else None
+                run = done - first if d["done"] and first >= 0 and done >= first else None
+                d["pixel_slices_per_s"] = (d["pixel_slices"] / run
+                                           if run and d["status"] == 0 else None)
+                if extra and rid in extra:
+                    d.update(extra[rid])
+                fh.write(json.dumps(d) + "\n")
 
     def stats(self) -> dict:
         s = ServerStats()

@@ -31,6 +31,9 @@ struct eels_ctx {
   int batch_sites = 0;                    // cap on sites per contraction batch (0: by memory)
   int wait_test = 0;                      // failure test: short pipeline waits, loads withheld
   int check_test = 0;                     // bounds-checked build test: a bad window origin
+  // flops of the last map's contraction as grouped (8 per complex product, one product per
+  // complex multiply-add whatever the operand split), for per-request metrics
+  double last_map_flops = 0;
   // called between tiles of work (after each slice of a build, after each depth of a map);
   // a non-zero return abandons the call with EELS_ERR_CANCELLED (the map server's gate)
   eels::TileHook hook = nullptr;
@@ -266,6 +269,8 @@ void eels::set_tile_hook(eels_ctx* ctx, TileHook fn, void* user) {
   ctx->hook = fn;
   ctx->hook_user = user;
 }
+
+double eels::last_map_flops(const eels_ctx* ctx) { return ctx ? ctx->last_map_flops : 0.0; }
 
 extern "C" {
 
@@ -665,6 +670,7 @@ eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transit
                        double* map_out, int map_on_device, void* stream) {
   eels_status r = EELS_OK;
   bool nonfinite = false;
+  ctx->last_map_flops = 0;
   const bool tc = precision != EELS_PREC_FP32;
   const int tc_prec = precision == EELS_PREC_BF16X3 ? EELS_TC_BF16X3 : EELS_TC_TF32;
   EELS_CK(enter(ctx));
@@ -819,10 +825,9 @@ eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transit
   // AUTO: measured once per shape (both groupings timed on the first occupied slice)
   const std::vector<int64_t> shape_key = {tc_prec, n, n_out, n_in, w, nr_cap, T};
   int chosen = ctx->assoc;
-  if (chosen == EELS_ASSOC_MODEL) {
-    // complex products of each grouping over the map's sites (Eq. SHn0 applied to the
-    // probes): the smaller one, with no timing, so the choice never depends on load
-    double c_tr = 0, c_pr = 0;
+  // complex products of each grouping over the map's sites (Eq. SHn0 applied to the probes)
+  double c_tr = 0, c_pr = 0;
+  {
     const double P2 = (double)w * w;
     for (int s = 0; s < S; ++s) {
       const double nr = (double)L.xcnt[s] * L.ycnt[s];
@@ -830,8 +835,9 @@ eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transit
       c_tr += T * ((double)n_out * P2 * n_in + (double)n_out * n_in * nr);
       c_pr += nr * n_in * P2 + T * (double)n_out * P2 * nr;
     }
-    chosen = c_pr <= c_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
   }
+  if (chosen == EELS_ASSOC_MODEL)   // the smaller one, with no timing: never load-dependent
+    chosen = c_pr <= c_tr ? EELS_ASSOC_PROBE_FIRST : EELS_ASSOC_TRANSITION_FIRST;
   // tile widths: the narrow tile when it covers the GEMM's columns with at least 5 % fewer
   // padded columns (the rule when nothing is measured); per grouping, first and second GEMM
   auto padded = [](int64_t cols, int64_t wd) { return (cols + wd - 1) / wd * wd; };
@@ -1240,6 +1246,7 @@ eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transit
   // I = f^2 (f^2/n_in) (4/N^2)^2 sum |M_gpu a_gpu|^2: S-matrices are stored scaled
   // by N, S_out carries the factor 4 of the half-grid inner product, and the probe
   // coefficients carry c = f/sqrt(n_in).
+  ctx->last_map_flops = 8.0 * ((tc && chosen == EELS_ASSOC_PROBE_FIRST) ? c_pr : c_tr);
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
   // device status: bit 1 a bounded tensor-core wait timed out, bit 2 the map holds NaN or

@@ -15,6 +15,8 @@ namespace eels {
 // EELS_ERR_CANCELLED.  The map server installs one on each of its contexts.
 typedef int (*TileHook)(void* user, int phase, int done, int total);
 void set_tile_hook(eels_ctx* ctx, TileHook fn, void* user);
+// Flops of the context's last map contraction as grouped (8 per complex product).
+double last_map_flops(const eels_ctx* ctx);
 
 // True if the multislice kernels are compiled for grid side n.
 bool grid_supported(int n);

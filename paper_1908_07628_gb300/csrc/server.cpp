@@ -49,6 +49,9 @@ struct Request {
   eels_request in{};              // borrowed input pointers
   int64_t footprint = 0;
   int64_t pixel_slices = 0;
+  int n_in = 0, n_out = 0;        // probe and detector beams
+  int64_t wave_steps = 0;         // multislice wave-slice steps the request issues
+  double flops = 0;               // the map's contraction flops, once it has finished
   std::vector<double> map;
   eels_status status = EELS_OK;
   std::string err;
@@ -156,6 +159,11 @@ void run_request(eels_server* sv, Request* r) {
         s = eels_inelastic_map(ctx, sm, &r->in.tr, &r->in.scan, r->in.beta, r->in.precision,
                                r->map.data(), 0, r->st);
       if (s != EELS_OK) r->err = eels_last_error(ctx);
+      const double flops = s == EELS_OK ? eels::last_map_flops(ctx) : 0.0;
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        r->flops = flops;
+      }
       eels_smatrix_free(sm);
     }
   } else {
@@ -269,6 +277,9 @@ eels_status eels_server_submit(eels_server* sv, const eels_request* q, int64_t* 
   r->sv = sv;
   r->footprint = fp;
   r->pixel_slices = (int64_t)q->scan.n_sx * q->scan.n_sy * q->spec.n_z;
+  r->n_in = beams(in.spec.n, in.spec.cell, in.optics.lambda, in.optics.f, in.optics.alpha);
+  r->n_out = beams(in.spec.n, in.spec.cell, in.optics.lambda, in.optics.f, in.beta);
+  r->wave_steps = ((int64_t)r->n_in * (in.sin_checkpoint >= 2 ? 2 : 1) + r->n_out) * in.spec.n_z;
   r->map.assign((size_t)q->tr.n_types * q->scan.n_sx * q->scan.n_sy, 0.0);
   {
     std::lock_guard<std::mutex> lock(sv->mu);
@@ -336,6 +347,11 @@ eels_status eels_server_request_info(eels_server* sv, int64_t id, eels_request_i
   out->t_done = r->done ? r->t_done - sv->t0 : -1;
   out->tiles = r->tiles;
   out->footprint = r->footprint;
+  out->n_in = r->n_in;
+  out->n_out = r->n_out;
+  out->pixel_slices = r->pixel_slices;
+  out->wave_steps = r->wave_steps;
+  out->contraction_flops = r->flops;
   return EELS_OK;
 }
 

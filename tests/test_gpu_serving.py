@@ -138,3 +138,52 @@ def test_cancelled_and_expired_requests_are_dropped(g):
     ctx = g.Context(0)
     for (wl, prec), got in zip(reqs, maps):
         assert ms.relative_error(_alone(g, ctx, wl, prec), got) < SAME, prec
+
+
+def _window_count(coords, positions, cell, f):
+    """Scan positions within a site's PRISM window along one axis (minimum image, half-open
+    [-L/2f, L/2f))."""
+    out = []
+    for s in coords:
+        d = s - positions
+        d = d - cell * np.floor(d / cell + 0.5)
+        out.append(int(np.sum((d >= -cell / (2 * f)) & (d < cell / (2 * f)))))
+    return np.array(out)
+
+
+def test_request_metrics_and_jsonl_log(g, tmp_path):
+    """Per-request metrics: beams, pixel-slices, wave-steps (with and without S_in
+    checkpoints) and the contraction's flops as the server groups it (8 per complex
+    product, the grouping with fewer products), and one JSON line per request."""
+    import json
+    reqs = _requests()[:3]
+    built = [_req(g, wl, prec, sin_checkpoint=3 if k == 1 else 0)
+             for k, (wl, prec) in enumerate(reqs)]
+    srv = g.Server(0, hbm_budget=sum(g.request_footprint(r) for r, _ in built), slots=2)
+    ids = [srv.submit(r, keep, wl.n_types, wl.scan) for (r, keep), (wl, _) in zip(built, reqs)]
+    for i in ids:
+        srv.wait(i, timeout=300)
+    infos = [srv.info(i) for i in ids]
+    path = str(tmp_path / "requests.jsonl")
+    srv.log_jsonl(path, ids, extra={ids[0]: {"tag": "first"}})
+    srv.close()
+    for k, ((wl, prec), d) in enumerate(zip(reqs, infos)):
+        n_in = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)
+        n_out = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.beta)
+        assert (d["n_in"], d["n_out"]) == (n_in, n_out)
+        n_sx, n_sy, x0, y0, sx, sy = wl.scan
+        assert d["pixel_slices"] == n_sx * n_sy * wl.n_z
+        assert d["wave_steps"] == (n_in * (2 if k == 1 else 1) + n_out) * wl.n_z
+        nx = _window_count(wl.site_x, x0 + sx * np.arange(n_sx), wl.cell, wl.f)
+        ny = _window_count(wl.site_y, y0 + sy * np.arange(n_sy), wl.cell, wl.f)
+        nr = (nx * ny).astype(float)
+        P, T = wl.H.shape[-1] ** 2, wl.n_types
+        c_tr = float(np.sum((nr > 0) * T * (n_out * P * n_in + n_out * n_in * nr)))
+        c_pr = float(np.sum(nr * n_in * P + T * n_out * P * nr))
+        want = 8 * (c_tr if prec == "fp32" else min(c_tr, c_pr))
+        assert want > 0 and abs(d["contraction_flops"] - want) <= 1e-9 * want, (prec, d, want)
+    lines = [json.loads(ln) for ln in open(path)]
+    assert [ln["id"] for ln in lines] == ids and lines[0]["tag"] == "first"
+    for ln in lines:
+        assert ln["status"] == 0 and ln["latency_s"] > 0 and ln["pixel_slices_per_s"] > 0
+        assert ln["wait_s"] >= 0 and ln["contraction_flops"] > 0
