@@ -675,6 +675,17 @@ def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
                   "frac": alg[k][1] / sec / 1e9 / peaks["hbm_gbs"],
                   "fft_tflops": fft[k] / sec / 1e12,
                   "fp32_frac": fft[k] / sec / 1e12 / tpk["fp32_fma_tflops"]}
+    # the whole slice step (row + column pass) against the minimum bytes a beam-step must
+    # move: read and write the band-limited state, 2 (N/2)^2 complex64, plus the S store,
+    # (N/2)^2 (the two-pass design moves about three times that)
+    min_b = 3 * (wl.n // 2) ** 2 * 8
+    for name, waves, r, c in (("forward_step", n_in, "row_pass", "col_pass"),
+                              ("adjoint_step", n_out, "row_pass_adjoint", "col_pass_adjoint")):
+        if r in prof and c in prof and prof[r]["ms"] + prof[c]["ms"] > 0:
+            sec = (prof[r]["ms"] + prof[c]["ms"]) / steps / 1e3
+            gbs = waves * wl.n_z * min_b / sec / 1e9
+            out[name + "_vs_min_bytes"] = {"min_bytes_per_beam_step": min_b,
+                                           "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
     return out
 
 
@@ -730,6 +741,8 @@ def gpu_arm(args, rank, world, ref_samples):
     precision = args.precision or CONFIG_PRECISION.get(args.workload, "bf16x3")
     ctx = g.Context(dev)
     ctx.set_association(args.association)
+    if args.operand_mib:
+        ctx.set_operand_budget(args.operand_mib)
     ctx.set_sout_scheme(args.sout_scheme)
     stream = torch.cuda.current_stream()
     n_in = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)
@@ -1126,6 +1139,9 @@ def main():
                     help="append one JSON line per serving request to this file")
     ap.add_argument("--serving-load", type=float, default=1.5,
                     help="offered load of the request stream, as a multiple of the service rate")
+    ap.add_argument("--operand-mib", type=int, default=0,
+                    help="device memory (MiB) for one batch's tensor-core operands (0: the "
+                         "library's default); small profiling captures")
     ap.add_argument("--max-slices", type=int, default=0,
                     help="keep only the first K slices (smaller device footprint for profiling)")
     args = ap.parse_args()

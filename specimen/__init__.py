@@ -459,6 +459,28 @@ def nanoparticle_small_1024():
                     site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=wl.scan)
 
 
+def nanoparticle_centre_512():
+    """The four central slices (46-54 A deep) of the 80 A Fe-O sphere in its 100 A box on
+    a 512^2 grid, f = 4, 64x64 scan over 80 A: the headline's contraction shapes (n_in,
+    n_out and the 24-pixel windows depend on the box, not the grid) in a few GB, for
+    profiling the GEMMs."""
+    a, box, n, f, w = A_FEO, 100.0, 512, 4, 24
+    dz, z0, n_z = 2.0, 46.0, 4
+    x, y, z, sp = nanoparticle_atoms(a, 80.0, box)
+    lay = np.floor((z - z0) / dz + 1e-9).astype(np.int32)
+    keep = (lay >= 0) & (lay < n_z)
+    x, y, sp, lay = x[keep], y[keep], sp[keep], lay[keep]
+    vproj = projected_potentials(n, box, n_z, x, y, sp, lay)
+    fe = sp == "Fe"
+    H, wx, wy = transition_windows(n, box, w, x[fe], y[fe])
+    scan = (64, 64, 10.0, 10.0, 80.0 / 64, 80.0 / 64)
+    return Workload(name="feo_sphere80_n512_f4_centre4", n=n, cell=box, n_z=n_z, dz=dz,
+                    lam=LAM_200KEV, sigma=interaction_constant(200e3, LAM_200KEV), f=f,
+                    alpha=0.020, beta=0.030, vproj=vproj, w=w, H=H,
+                    site_slice=lay[fe].astype(np.int32), site_x=x[fe].copy(),
+                    site_y=y[fe].copy(), win_x0=wx, win_y0=wy, scan=scan)
+
+
 WORKLOADS = {
     "rocksalt_small": rocksalt_small,
     "rocksalt_fp32": rocksalt_fp32,
@@ -466,6 +488,7 @@ WORKLOADS = {
     "nanoparticle": nanoparticle,
     "nanoparticle_small": nanoparticle_small,
     "nanoparticle_small_1024": nanoparticle_small_1024,
+    "nanoparticle_centre_512": nanoparticle_centre_512,
 }
 
 
