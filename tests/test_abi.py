@@ -43,6 +43,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_symbols()) == set(lib.EXPORTS)
 
 
+def test_checked_build_compiles_and_exports_the_same_symbols(lib):
+    """The bounds-checked variant (-DSTEM_CHECK) builds beside the normal library, says so
+    through eels_checked_build, and exports every declared entry point; the normal
+    library says it is not checked."""
+    import ctypes
+    from paper_1908_07628_gb300 import build
+    path = build.build(check=True)
+    assert path == build.lib_path(True) and path != lib.LIB_PATH
+    checked, normal = ctypes.CDLL(path), ctypes.CDLL(lib.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(checked, name), name
+    assert checked.eels_checked_build() == 1 and normal.eels_checked_build() == 0
+
+
 def test_beam_counts_match_oracle_enumeration(lib):
     """Integer work: the library's aperture enumeration equals the oracle's exactly."""
     for (n, L, f, ang) in [(128, 8.6, 1, 0.02), (128, 8.6, 1, 0.03), (512, 34.4, 2, 0.02),
