@@ -287,6 +287,31 @@ def test_large_workloads_sampled(g, ctx, name, targets, probes):
         assert eps(r, t) < EPS[prec], (prec, assoc, eps(r, t))
 
 
+def test_headline_map_is_additive_over_its_sites(g, ctx):
+    """The 1024^2 nanoparticle with all 13 571 sites, in the launch configuration the
+    bench times (BF16 hi + lo, probe-first, batches of about 90 sites, several batches per
+    slice): the map is a sum over sites (Eq. SHn0 summed over transitions), so the maps
+    of the even- and odd-numbered sites add up to the full map, up to FP64 summation
+    order (grouping and tile width fixed so that every site's contribution is computed
+    the same way in all three calls).  The full map is finite and positive wherever a
+    probe sees a site."""
+    wl = sp.nanoparticle()
+    sm = g.build_smatrix_for(ctx, wl)
+    ctx.set_association("probe_first")
+    ctx.set_tile_width(256)
+    try:
+        full = g.inelastic_map_for(ctx, sm, wl, "bf16x3")
+        even = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(0, wl.n_sites, 2)), "bf16x3")
+        odd = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(1, wl.n_sites, 2)), "bf16x3")
+    finally:
+        ctx.set_association("auto")
+        ctx.set_tile_width(0)
+    del sm
+    assert np.all(np.isfinite(full)) and full.min() >= 0 and full.max() > 0
+    assert np.abs(even + odd - full).max() <= 1e-12 * full.max()
+    assert even.max() > 0 and odd.max() > 0
+
+
 @pytest.mark.parametrize("cap", [1, 3])
 def test_several_batches_per_slice_match_oracle(g, ctx, cap):
     """Sites of one slice contracted in several batches (EELS_OPT_BATCH_SITES): the
