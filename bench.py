@@ -240,13 +240,27 @@ def _algorithmic(wl, n_in, n_out, prof, steps):
     last = (n * nh + nh * nh) * c
     col = 2 * n * nh * c
     t = n * n * c
+    work = work_depths(wl)
+    # the backward sweep stores S_out only at depths with transitions (and skips the
+    # depth-0 pass when that depth has none)
+    adj = sum((2 * n * nh + (nh * nh if i in work else 0)) * c for i in range(1, nz)) + \
+        (last if 0 in work else 0)
     out = {}
-    for name, waves in (("row_pass", n_in), ("row_pass_adjoint", n_out)):
+    for name, waves, per_wave in (("row_pass", n_in, (nz - 1) * row + last),
+                                  ("row_pass_adjoint", n_out, adj)):
         launches = prof.get(name, {}).get("launches", 0) / steps
-        out[name] = ("hbm", waves * ((nz - 1) * row + last) + launches * t)
+        out[name] = ("hbm", waves * per_wave + launches * t)
     for name, waves in (("col_pass", n_in), ("col_pass_adjoint", n_out)):
         out[name] = ("hbm", waves * (nz - 1) * col)
     return out
+
+
+def work_depths(wl):
+    """Depths whose sites some probe of the scan reaches (the map contracts only those)."""
+    rx, ry = wl.scan_positions()
+    return {int(wl.site_slice[s]) for s in range(wl.n_sites)
+            if _window_count(wl.site_x[s], rx, wl.cell, wl.f) and
+            _window_count(wl.site_y[s], ry, wl.cell, wl.f)}
 
 
 def crop_study(g, ctx, stream, widths=(64, 48, 30, 22, 15), reps=3):
@@ -662,8 +676,9 @@ def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
     nn = float(wl.n) ** 2
     row_full, row_last = 10 * nn * lg + 6 * nn, 5 * nn * lg + 6 * nn
     col = 5 * nn * lg + 3 * nn
+    work = work_depths(wl)
     fft = {"row_pass": n_in * ((wl.n_z - 1) * row_full + row_last),
-           "row_pass_adjoint": n_out * ((wl.n_z - 1) * row_full + row_last),
+           "row_pass_adjoint": n_out * ((wl.n_z - 1) * row_full + (row_last if 0 in work else 0)),
            "col_pass": n_in * (wl.n_z - 1) * col,
            "col_pass_adjoint": n_out * (wl.n_z - 1) * col}
     out = {}
@@ -678,13 +693,15 @@ def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
     # the whole slice step (row + column pass) against the minimum bytes a beam-step must
     # move: read and write the band-limited state, 2 (N/2)^2 complex64, plus the S store,
     # (N/2)^2 (the two-pass design moves about three times that)
-    min_b = 3 * (wl.n // 2) ** 2 * 8
-    for name, waves, r, c in (("forward_step", n_in, "row_pass", "col_pass"),
-                              ("adjoint_step", n_out, "row_pass_adjoint", "col_pass_adjoint")):
+    state, store = 2 * (wl.n // 2) ** 2 * 8, (wl.n // 2) ** 2 * 8
+    for name, waves, r, c, stores in (
+            ("forward_step", n_in, "row_pass", "col_pass", wl.n_z),
+            ("adjoint_step", n_out, "row_pass_adjoint", "col_pass_adjoint", len(work))):
         if r in prof and c in prof and prof[r]["ms"] + prof[c]["ms"] > 0:
             sec = (prof[r]["ms"] + prof[c]["ms"]) / steps / 1e3
-            gbs = waves * wl.n_z * min_b / sec / 1e9
-            out[name + "_vs_min_bytes"] = {"min_bytes_per_beam_step": min_b,
+            total = waves * (wl.n_z * state + stores * store)
+            gbs = total / sec / 1e9
+            out[name + "_vs_min_bytes"] = {"min_bytes_per_beam_step": total / (waves * wl.n_z),
                                            "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
     return out
 

@@ -1177,10 +1177,12 @@ eels_status map_window(eels_ctx* ctx, const eels_smatrix* sm, const eels_transit
     for (int i = n_z - 1; i >= 0; --i) {
       if (sm->ckpt && (i == n_z - 1 || (i + 1) % K == 0) && has_work_to(i))
         if ((rs = recompute_segment(i)) != EELS_OK) return rs;
-      // S_out(i) = N Dec beta(i); then conj(t_i) and the forward x-FFT for level i-1
-      {
+      // S_out(i) = N Dec beta(i), stored only where depth i holds transitions; then
+      // conj(t_i) and the forward x-FFT for level i-1
+      const int store = has_work(i) ? 2 : 0;
+      if (store || i > 0) {
         Prof pr(ctx, "row_pass_adjoint", st);
-        EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, t_of(i), 1, 2, Sout.p, n_out, plane,
+        EELS_CK(launch_row_pass(n, n_out, W.p, Phi.p, t_of(i), 1, store, Sout.p, n_out, plane,
                                 i > 0 ? 1 : 0, tw, st));
       }
       if ((rs = contract_depth(i)) != EELS_OK) return rs;
