@@ -655,15 +655,18 @@ def _roofline(dom, wl, n_in, n_out, prof, steps, peaks, tpk, clk):
         # the step runs for seconds: the sustained figure (measured under the power cap)
         return _tensor_roof(dom, wl, n_in, n_out, prof, steps, peaks["bf16_tflops_sustained"],
                             "measured bf16 sustained (MEASURED_PEAKS.json)")
+    nominal = tpk.get("nominal", False)   # --no-peaks: nominal ratios, not measured
     if "tf32" in dom:
         return _tensor_roof(dom, wl, n_in, n_out, prof, steps, tpk["tf32_tflops_sustained"],
-                            "measured tf32 sustained (cuBLAS, this run)")
+                            "nominal: measured bf16 sustained x 1.1/2.25 (--no-peaks)" if nominal
+                            else "measured tf32 sustained (cuBLAS, this run)")
     flops = contraction_flops(wl, n_in, n_out, dom)
     peak = tpk["fp32_fma_tflops"]
     achieved = flops / per_step / avg_s / 1e12
     return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3,
-            "peak_source": "measured fp32 FMA rate (eels_fp32_fma_rate, this run)"}
+            "peak_source": "nominal: 152 x 128 x 2 x max clock (--no-peaks)" if nominal
+            else "measured fp32 FMA rate (eels_fp32_fma_rate, this run)"}
 
 
 def _multislice_bounds(wl, n_in, n_out, prof, steps, peaks, tpk):
@@ -804,7 +807,8 @@ def gpu_arm(args, rank, world, ref_samples):
             tpk = {"tf32_tflops": peaks["bf16_tflops"] * 1.1 / 2.25,
                    "tf32_tflops_sustained": peaks["bf16_tflops_sustained"] * 1.1 / 2.25,
                    "fp32_fma_tflops": 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6,
-                   "how": "not measured (--no-peaks): bf16 x 1.1/2.25 and 152 x 128 x 2 x clock"}
+                   "how": "not measured (--no-peaks): bf16 x 1.1/2.25 and 152 x 128 x 2 x clock",
+                   "nominal": True}
         else:
             tpk = measure_peaks(g, dev)
         tot = {k: v["ms"] for k, v in prof.items()}
