@@ -287,22 +287,25 @@ def test_large_workloads_sampled(g, ctx, name, targets, probes):
         assert eps(r, t) < EPS[prec], (prec, assoc, eps(r, t))
 
 
-def test_headline_map_is_additive_over_its_sites(g, ctx):
-    """The 1024^2 nanoparticle with all 13 571 sites, in the launch configuration the
-    bench times (BF16 hi + lo, probe-first, batches of about 90 sites, several batches per
-    slice): the map is a sum over sites (Eq. SHn0 summed over transitions), so the maps
+@pytest.mark.parametrize("name,prec", [("nanoparticle", "bf16x3"),
+                                       ("rocksalt_vacancy", "bf16x3"),
+                                       ("rocksalt_fp32", "tf32")])
+def test_full_size_map_is_additive_over_its_sites(g, ctx, name, prec):
+    """The full-size workloads with all their sites (13 571 on the 1024^2 nanoparticle,
+    21 835 on the 768^2 vacancy crystal, 5 120 on the 512^2 crystal), in the launch
+    configuration the bench times (batches of tens of sites, several per slice on the
+    sphere): the map is a sum over sites (Eq. SHn0 summed over transitions), so the maps
     of the even- and odd-numbered sites add up to the full map, up to FP64 summation
     order (grouping and tile width fixed so that every site's contribution is computed
-    the same way in all three calls).  The full map is finite and positive wherever a
-    probe sees a site."""
-    wl = sp.nanoparticle()
+    the same way in all three calls).  The full map is finite and non-negative."""
+    wl = sp.WORKLOADS[name]()
     sm = g.build_smatrix_for(ctx, wl)
     ctx.set_association("probe_first")
     ctx.set_tile_width(256)
     try:
-        full = g.inelastic_map_for(ctx, sm, wl, "bf16x3")
-        even = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(0, wl.n_sites, 2)), "bf16x3")
-        odd = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(1, wl.n_sites, 2)), "bf16x3")
+        full = g.inelastic_map_for(ctx, sm, wl, prec)
+        even = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(0, wl.n_sites, 2)), prec)
+        odd = g.inelastic_map_for(ctx, sm, wl.with_sites(np.arange(1, wl.n_sites, 2)), prec)
     finally:
         ctx.set_association("auto")
         ctx.set_tile_width(0)
