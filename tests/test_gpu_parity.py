@@ -397,6 +397,32 @@ def test_checkpointed_s_in_gives_the_same_map(g, ctx, k):
         ctx.set_sout_scheme("stream")
 
 
+def test_headline_checkpointed_s_in_gives_the_same_map(g, ctx):
+    """The 1024^2 sphere with every site, S_in kept only as probe waves every 8 slices (the
+    map server's choice for requests whose S-matrices would not fit, here 36 GB of
+    checkpoints instead of 131 GB): the map recomputed segment by segment equals the map
+    from the stored S_in up to FP64 summation order."""
+    wl = sp.nanoparticle()
+    ctx.set_association("probe_first")
+    ctx.set_tile_width(256)
+    try:
+        sm = g.build_smatrix_for(ctx, wl)
+        whole = g.inelastic_map_for(ctx, sm, wl, "bf16x3")
+        del sm
+        ctx.set_sin_checkpoint(8)
+        try:
+            smc = g.build_smatrix_for(ctx, wl)
+        finally:
+            ctx.set_sin_checkpoint(0)
+        got = g.inelastic_map_for(ctx, smc, wl, "bf16x3")
+        del smc
+    finally:
+        ctx.set_association("auto")
+        ctx.set_tile_width(0)
+    assert whole.max() > 0
+    assert np.abs(got - whole).max() <= 1e-12 * whole.max()
+
+
 # --- failure detection: a bounded device wait that runs out ------------------------------
 
 def test_bounded_wait_timeout_is_reported_and_context_recovers(g, ctx):
