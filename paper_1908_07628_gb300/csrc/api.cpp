@@ -181,7 +181,7 @@ cudaError_t collect_checks(int* status, cudaStream_t st) {
 // The same for calls without a status word of their own: EELS_ERR_BOUNDS if a kernel's
 // check failed since the flags were last collected.  The flags are per process, so a
 // violation is reported by the next checked call on any context.
-eels_status bounds_verdict(eels_ctx* ctx, cudaStream_t st) {
+eels_status checked_status(eels_ctx* ctx, cudaStream_t st) {
 #ifdef STEM_CHECK
   DevBuf<int> flag;
   EELS_CK(flag.alloc(1, st));
@@ -564,7 +564,7 @@ eels_status eels_build_smatrix(eels_ctx* ctx, const eels_specimen* spec, const e
     e = launch_row_pass(n, n_in, W.p, nullptr, sm->t, 0, 2, sm->s_exit, n_in, plane, 0, tw, st);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "exit plane store"));
   }
-  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return bail(r);
+  if ((r = checked_status(ctx, st)) != EELS_OK) return bail(r);
   *out = sm;
   return EELS_OK;
 }
@@ -1437,7 +1437,7 @@ eels_status eels_elastic_images(eels_ctx* ctx, const eels_smatrix* sm, const eel
   const double nn = (double)n * (double)n;
   const double scale = (double)f * f * ((double)f * f / n_in) * 16.0 / (nn * nn);
   EELS_CK(eels::launch_scale(dimg.p, n_det * n_img, scale, st));
-  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return r;
+  if ((r = checked_status(ctx, st)) != EELS_OK) return r;
   if (out_on_device) {
     EELS_CK(cudaMemcpyAsync(out, dimg.p, sizeof(double) * n_det * n_img, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -1657,7 +1657,7 @@ eels_status eels_quadratic_reference_map(eels_ctx* ctx, const eels_specimen* spe
     k0 = k1;
   }
   if (steps) *steps = total_steps;
-  if ((r = bounds_verdict(ctx, st)) != EELS_OK) return r;
+  if ((r = checked_status(ctx, st)) != EELS_OK) return r;
   if (map_on_device) {
     EELS_CK(cudaMemcpyAsync(map_out, dmap.p, sizeof(double) * n_map, cudaMemcpyDeviceToDevice, st));
   } else {
