@@ -175,6 +175,40 @@ def test_single_slice_and_extreme_windows(g, ctx):
             assert eps(ref, got) < EPS[prec], (w, prec, assoc)
 
 
+@pytest.mark.parametrize("n_types", [1, 6])
+def test_channel_counts(g, ctx, n_types):
+    """One channel and six (the serving stream's range): the per-channel planes of the
+    spread epilogue, the transition lists and the map planes, in every variant."""
+    wl = _rand(128, 2, 43, n_sites=5, w=12, n_types=n_types)
+    ref = ms.quadratic_map(wl)
+    assert ref.shape[0] == n_types and ref.max() > 0
+    sm = g.build_smatrix_for(ctx, wl)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, wl, prec, assoc)
+        assert eps(ref, got) < EPS[prec], (n_types, prec, assoc)
+        for m in range(n_types):
+            if ref[m].max() > 0:
+                assert eps(ref[m], got[m]) < EPS[prec], (n_types, m, prec, assoc)
+
+
+@pytest.mark.parametrize("scan", [(1, 1), (7, 1), (1, 9)])
+def test_degenerate_scans(g, ctx, scan):
+    """A single probe position and single-row / single-column scans (one-row phase tables,
+    one-position windows, GEMM tiles with one valid column pair or row) in every variant."""
+    wl = _rand(128, 2, 41, n_sites=6, w=10, scan_n=4)
+    wl = wl.with_scan(scan + tuple(wl.scan[2:]))
+    ref = ms.quadratic_map(wl)
+    assert ref.shape[1:] == (scan[1], scan[0])
+    sm = g.build_smatrix_for(ctx, wl)
+    for prec, assoc in variants():
+        got = run_map(g, ctx, sm, wl, prec, assoc)
+        assert got.shape == ref.shape
+        if ref.max() == 0:
+            assert not got.any(), (prec, assoc)
+        else:
+            assert eps(ref, got) < EPS[prec], (scan, prec, assoc)
+
+
 def test_site_outside_every_window_contributes_nothing(g, ctx):
     wl = _rand(128, 4, 12, n_sites=4)
     rx, ry = wl.scan_positions()
