@@ -763,6 +763,8 @@ def gpu_arm(args, rank, world, ref_samples):
     ctx.set_association(args.association)
     if args.operand_mib:
         ctx.set_operand_budget(args.operand_mib)
+    if args.tile_width:
+        ctx.set_tile_width(args.tile_width)
     ctx.set_sout_scheme(args.sout_scheme)
     stream = torch.cuda.current_stream()
     n_in = g.count_beams(wl.n, wl.cell, wl.lam, wl.f, wl.alpha)
@@ -1160,6 +1162,8 @@ def main():
                     help="append one JSON line per serving request to this file")
     ap.add_argument("--serving-load", type=float, default=1.5,
                     help="offered load of the request stream, as a multiple of the service rate")
+    ap.add_argument("--tile-width", type=int, default=0, choices=[0, 128, 256],
+                    help="force the output tile width of the tensor-core GEMMs (0: chosen)")
     ap.add_argument("--operand-mib", type=int, default=0,
                     help="device memory (MiB) for one batch's tensor-core operands (0: the "
                          "library's default); small profiling captures")
